@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 AMR multigrid solve (libafgpu through its C ABI).
+
+Metric: unknowns per second to a 1e-8 relative residual (max|rho - A u| /
+max|rho| over leaf cells), FAS FMG + V(2,2) cycles with red-black
+Gauss-Seidel (Teunissen & Ebert, arXiv:1701.04329 Sec. 3), on the 3D octree
+workload: [0,1]^3, boxes of 8^3 cells, uniform 256^3 (level 6) plus two
+refinement levels around two Gaussian sources (s = 0.01, +1 at (.3,.5,.5),
+-1 at (.7,.5,.5)), u = 0 on the boundary (about 1.76e7 unknowns).  One step
+= set rhs and boundary data, zero initial guess, FMG + V-cycles until the
+tolerance, read the solution back.  `value` is the plain FP64 method; the
+`mixed` object is the FP32-multigrid + FP64-defect-correction solve of the
+same tree.  The working set (> 0.5 GB of field data) exceeds the 129 MB L2,
+so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl afgpu|reference]
+For N > 1 launch with torchrun; every rank solves its own replica (the
+single-tree solve has no natural shard), value = total unknowns/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknowns/s to 1e-8 rel. residual, FP64 vs FP32+FP64-refine; % of HBM peak"
+WORKLOAD = ("3D octree Poisson, boxes 8^3, uniform 256^3 (level 6) + 2 refinement levels around two "
+            "Gaussian sources (s=0.01, +-1), Dirichlet u=0; FMG + V(2,2) cycles, N_base=4, to rel. residual 1e-8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="afgpu", choices=["afgpu", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--uniform-level", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "MEASURED_PEAKS.json"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(problem, tol, steps=1):
+    """The oracle as it stands, on this host's cores: full solves to `tol`."""
+    from oracle.oracle import OracleTree
+    t = OracleTree(problem.dim, problem.box_n, problem.max_level)
+    problem.build(t)
+    rho, b = problem.data(t)
+    t.set_rhs(rho)
+    t.set_dirichlet(b)
+    times, cycles = [], 0
+    for _ in range(steps):
+        t.zero_solution()
+        t0 = time.perf_counter()
+        cycles = t.solve(tol, 60)
+        times.append(time.perf_counter() - t0)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return t.n_leaf_cells, times, cycles, cores
+
+
+def run_reference(args):
+    """--impl reference: the oracle (the only reference this build has) on the
+    host cores, same workload, metric and unit; rank 0 only."""
+    from paper_1701_04329_gb300 import workloads as W
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    p = W.twosrc3d(uniform_level=args.uniform_level)
+    from oracle.oracle import OracleTree
+    t = OracleTree(p.dim, p.box_n, p.max_level)
+    p.build(t)
+    rho, b = p.data(t)
+    t.set_rhs(rho)
+    t.set_dirichlet(b)
+    n = t.n_leaf_cells
+    for _ in range(args.warmup):
+        t.zero_solution()
+        t.solve(args.tol, 60)
+    t0 = time.perf_counter()
+    cyc = 0
+    for _ in range(args.steps):
+        t.zero_solution()
+        cyc = t.solve(args.tol, 60)
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = n / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": n, "cycles": cyc, "parallelism": "host cores (OpenMP over boxes)"},
+        "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+                         "sample": "full FP64 solve of the workload to rel. residual %g per step" % args.tol},
+        "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    from paper_1701_04329_gb300 import workloads as W
+
+    dist, rank, world, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk, pk_src = peaks()
+
+    p = W.twosrc3d(uniform_level=args.uniform_level)
+    tree = afgpu.Tree(p.dim, p.box_n, p.max_level)
+    p.build(tree)
+    info = tree.info()
+    n = info.n_leaf_cells
+    rho_h, b_h = p.data(tree)
+    rho = torch.tensor(rho_h, device=dev)
+    bv = torch.tensor(b_h, device=dev)
+    zero = torch.zeros(n, dtype=torch.float64, device=dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def make_step(opts):
+        def step():
+            tree.set_rhs(rho)
+            tree.set_dirichlet(bv)
+            tree.set_solution(zero)
+            st = tree.solve(opts)
+            tree.get_solution(out=u)
+            return st
+        return step
+
+    def timed(step, K, W_):
+        st = None
+        for _ in range(W_):
+            st = step()
+        torch.cuda.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = afgpu.kernel_launches()
+        e0.record()
+        for _ in range(K):
+            st = step()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize()
+        launches = afgpu.kernel_launches() - l0
+        ms = max_over_ranks(dist, e0.elapsed_time(e1) / K)
+        return ms, st, launches
+
+    opts64 = afgpu.default_opts(rel_tol=args.tol)
+    optsmx = afgpu.default_opts(rel_tol=args.tol, precision=afgpu.AFG_MIXED)
+    clocks = Clocks(local) if rank == 0 else None
+    ms64, st64, launches = timed(make_step(opts64), args.steps, args.warmup)
+    clk = clocks.stop() if clocks else None
+    u64 = u.clone()
+    msmx, stmx, launches_mx = timed(make_step(optsmx), args.steps, args.warmup)
+    umx = u.clone()
+    # reference solution for the error report: FP64 to 1e-12 (parity-tested against the oracle)
+    tree.set_solution(zero)
+    tree.solve(afgpu.default_opts(rel_tol=1e-12), allow_not_converged=True)
+    uref = tree.get_solution()
+    scale = float(uref.abs().max())
+    err64 = float((u64 - uref).abs().max()) / scale
+    errmx = float((umx - uref).abs().max()) / scale
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    rho_pin = torch.tensor(rho_h).pin_memory()
+    b_pin = torch.tensor(b_h).pin_memory()
+    u_pin = torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def e2e_step(opts):
+        def step():
+            rho.copy_(rho_pin, non_blocking=True)
+            bv.copy_(b_pin, non_blocking=True)
+            tree.set_rhs(rho)
+            tree.set_dirichlet(bv)
+            tree.set_solution(zero)
+            st = tree.solve(opts)
+            tree.get_solution(out=u)
+            u_pin.copy_(u, non_blocking=True)
+            return st
+        return step
+
+    ms_e2e, _, _ = timed(e2e_step(opts64), args.steps, 1)
+    ms_e2e_mx, _, _ = timed(e2e_step(optsmx), args.steps, 1)
+
+    # roofline: the dominant kernel (red-black half-sweep on the finest uniform level), timed alone
+    lvl = max(range(1, info.highest_level + 1), key=lambda l: info.boxes_per_level[l])
+    tree.set_rhs(rho)
+    probe = tree.time_kernel(4, 0, True, 3)
+    fp64_peak_tflops = probe["flops"] / (probe["ms"] * 1e-3) / 1e12
+    k64 = tree.time_kernel(0, lvl, True, 20)
+    k32 = tree.time_kernel(0, lvl, False, 20)
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    ach64 = k64["flops"] / (k64["ms"] * 1e-3) / 1e12
+    gbs64 = k64["bytes"] / (k64["ms"] * 1e-3) / 1e9
+    gbs32 = k32["bytes"] / (k32["ms"] * 1e-3) / 1e9
+
+    value = world * n / (ms64 * 1e-3)
+    vmx = world * n / (msmx * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": n, "boxes": info.n_boxes, "highest_level": info.highest_level,
+                   "cycles": st64["cycles"], "rel_residual": st64["rel_residual"],
+                   "err_vs_fp64_1e-12": err64, "l2": "working set > L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "k_smooth<3,8,double> (half-sweep, level %d)" % lvl,
+                     "achieved": ach64, "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": ach64 / fp64_peak_tflops,
+                     "peak_source": "FP64 FMA probe run in this process (FMA = 2 flops)",
+                     "ms": k64["ms"], "hbm_gbs": gbs64, "hbm_frac": gbs64 / hbm, "traffic": None},
+        "mixed": {"value": vmx, "unit": "unknowns/s", "ms_per_step": msmx, "dtype": "f32+f64",
+                  "cycles": stmx["cycles"], "rel_residual": stmx["rel_residual"], "err_vs_fp64_1e-12": errmx,
+                  "speedup_vs_fp64": ms64 / msmx, "gpu_launches": launches_mx,
+                  "e2e": {"value": world * n / (ms_e2e_mx * 1e-3), "unit": "unknowns/s"},
+                  "roofline": {"bound": "hbm", "kernel": "k_smooth<3,8,float> (half-sweep, level %d)" % lvl,
+                               "achieved": gbs32, "peak": hbm, "unit": "GB/s", "frac": gbs32 / hbm,
+                               "peak_source": pk_src + " (hbm_gbs, burst)", "ms": k32["ms"], "traffic": None}},
+        "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": "unknowns/s",
+                "h2d_bytes_per_step": int(rho_h.nbytes + b_h.nbytes), "d2h_bytes_per_step": int(n * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nc, times, cyc, cores = cpu_baseline(p, args.tol)
+        out["cpu_baseline"] = {"value": nc / min(times), "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+                               "sample": "one full FP64 solve of the same workload to rel. residual %g (%d cycles, %.1f s)"
+                                         % (args.tol, cyc, min(times))}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * afgpu.h -- C interface of libafgpu, a GB300 (sm_103a) implementation of
+ * the geometric multigrid method on quadtree/octree AMR grids of
+ * Teunissen & Ebert, "Afivo" (arXiv:1701.04329).
+ *
+ * Problem (Sec. 3, Eq. mg-discr-equation): A_h(u_h) = rho_h on [0,1]^D,
+ * D = 2 or 3, with Dirichlet data on the domain boundary, discretised on a
+ * tree of boxes of N^D cells (Sec. 1.3, 2.1).  The library holds the tree,
+ * its per-level box lists and all field data on the GPU; every operator of
+ * the solve (ghost cells, red-black Gauss-Seidel, residual, restriction,
+ * prolongation, norms) is a CUDA kernel of this library.
+ *
+ * Conventions
+ * -----------
+ * - Every function returns an int status (AFG_OK = 0 or a negative error);
+ *   afg_last_error() gives a message for the calling thread.  A call that
+ *   fails on its arguments leaves the handle unchanged.
+ * - Handles are opaque and not thread-safe; use one handle per host thread.
+ * - Tree-building calls (create, refine, adapt, cell/face centres, export)
+ *   work on HOST memory and need no GPU.
+ * - Field calls take DEVICE pointers (cudaMalloc'd or torch CUDA tensors).
+ *   They are enqueued on the handle's stream (afg_set_stream, default the
+ *   legacy default stream) and the pointers must stay valid until that work
+ *   has finished.  Calls returning host values (norms, stats) synchronise.
+ * - Leaf data order ("canonical"): leaf boxes by level ascending, Morton
+ *   order (x lowest bit) of the spatial index within a level; cells of a box
+ *   lexicographic with x fastest.  Boundary faces: leaf boxes in the same
+ *   order, sides -x,+x,-y,+y(,-z,+z), face cells lexicographic over the two
+ *   tangential axes, lower axis fastest.  For a forest, tree 0's data
+ *   first, then tree 1's, ...
+ * - After afg_adapt all field data on the tree is invalid (set it again).
+ */
+#ifndef AFGPU_H
+#define AFGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AFG_OK 0
+#define AFG_ERR_ARG (-1)            /* invalid argument */
+#define AFG_ERR_CUDA (-2)           /* a CUDA call failed (message names it) */
+#define AFG_ERR_NOMEM (-3)          /* allocation failed */
+#define AFG_ERR_STATE (-4)          /* call not valid in this state (e.g. no rhs set) */
+#define AFG_ERR_NOT_CONVERGED (-5)  /* max_cycles reached above rel_tol (results are valid) */
+#define AFG_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up */
+
+#define AFG_FP64 0   /* all multigrid arithmetic in double precision */
+#define AFG_MIXED 1  /* FP64 residual + update around FP32 multigrid (defect correction) */
+
+typedef struct afg_tree afg_tree;
+typedef struct afg_forest afg_forest;
+
+typedef struct {
+    int n_down;        /* smoothing steps before restriction (Sec. 3.2, default 2) */
+    int n_up;          /* smoothing steps after correction (default 2) */
+    int n_base;        /* relaxation steps on the coarsest grid (default 4) */
+    int max_cycles;    /* cycle limit for afg_solve / adjoint iterations (default 50) */
+    double rel_tol;    /* stop when max|rho - A u| / max|rho| <= rel_tol (default 1e-10) */
+    int precision;     /* AFG_FP64 or AFG_MIXED */
+    int inner_vcycles; /* AFG_MIXED: FP32 V-cycles per outer FP64 step (default 1) */
+    int use_graph;     /* 1: replay the cycle as a CUDA graph (default 1) */
+} afg_mg_opts;
+
+typedef struct {
+    int cycles;            /* cycles done (FMG counts as one) */
+    double rel_residual;   /* last max|r| / max|rho| */
+    double max_residual;   /* last max|r| */
+    double max_rho;        /* max|rho| over leaves */
+    double seconds;        /* wall time of the call (device-synchronised) */
+    double history[64];    /* rel_residual after each cycle, first 64 */
+} afg_stats;
+
+typedef struct {
+    int dim, box_n, max_level;
+    int highest_level;      /* finest level present */
+    int n_boxes, n_leaves;  /* tree boxes (levels >= 1) */
+    long long n_leaf_cells; /* unknowns */
+    long long n_bfaces;     /* leaf faces on the domain boundary */
+    int boxes_per_level[32];
+    int leaves_per_level[32];
+} afg_tree_info;
+
+/* Defaults of Sec. 3.2 / 4.1: N_down = N_up = 2, N_base = 4. */
+void afg_default_opts(afg_mg_opts *opts);
+
+const char *afg_last_error(void);
+
+/* ---- tree (Sec. 2.1-2.3) ------------------------------------------------ */
+
+/* Create a tree on [0,1]^dim with one root box of box_n^dim cells (level 1).
+ * dim in {2,3}; box_n in {4,8,16}; 1 <= max_level <= 21 (3D) or 30 (2D). */
+int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out);
+int afg_tree_destroy(afg_tree *t);
+
+/* CUDA stream (cudaStream_t) for all device work of this tree; NULL = default. */
+int afg_set_stream(afg_tree *t, void *cuda_stream);
+
+/* Refine every leaf until all leaves are at least on `level` (Sec. 1.3). */
+int afg_refine_uniform(afg_tree *t, int level);
+
+/* Leaf cell centres, canonical order, dim doubles per cell (host memory). */
+int afg_cell_centers(const afg_tree *t, double *xyz_host);
+
+/* Centres of the leaf boundary faces, canonical face order (host memory). */
+int afg_face_centers(const afg_tree *t, double *xyz_host);
+
+/* Level of every leaf box, canonical order (host memory). */
+int afg_leaf_levels(const afg_tree *t, int32_t *levels_host);
+
+/* Mesh adaptation (Sec. 2.3).  flags: one int8 per leaf cell in canonical
+ * order, +1 refine, 0 keep, -1 derefine (host memory).  Rules: a box with a
+ * flagged cell is refined (not beyond max_level); same-level leaves,
+ * diagonal ones included, within n_buf cells of such a cell are refined too;
+ * coarser neighbours of a refined box are refined for 2:1 balance (faces,
+ * edges and corners); the 2^D children of a box are removed when all their
+ * cells are flagged -1, none of them is refined, and no same-level
+ * neighbour of the box has a child that is or becomes refined.  The level
+ * changes by at most one per call.  0 <= n_buf <= box_n. */
+int afg_adapt(afg_tree *t, const int8_t *flags_host, int n_buf, int *n_added, int *n_removed);
+
+int afg_info(const afg_tree *t, afg_tree_info *out);
+
+/* Tree arrays in canonical box order (host memory): level[n], spatial index
+ * idx[n*dim] (1-based, Sec. 2.1), parent[n], children[n*2^dim] (child c has
+ * offset bit a = (c>>a)&1), neighbours[n*(3^dim-1)] in lexicographic
+ * (dz,dy,dx) order with x fastest, centre skipped.  -1 = no box, -2 =
+ * physical boundary.  Any pointer may be NULL. */
+int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *parent,
+                    int32_t *children, int32_t *neighbours);
+
+/* ---- fields (device memory, enqueued on the tree's stream) ------------- */
+
+/* Source term rho on leaf cells (n_leaf_cells doubles). */
+int afg_set_rhs(afg_tree *t, const double *rho_leaf_dev);
+/* Dirichlet values at the leaf boundary face centres (n_bfaces doubles);
+ * the ghost value is 2 b - u (Sec. 2.4).  Coarse boxes use face averages.
+ * Without this call the boundary data is zero. */
+int afg_set_dirichlet(afg_tree *t, const double *b_face_dev);
+/* Initial guess / warm start on leaf cells; without it the guess is zero. */
+int afg_set_solution(afg_tree *t, const double *u_leaf_dev);
+int afg_get_solution(const afg_tree *t, double *u_leaf_dev);
+
+/* ---- multigrid (Sec. 3) -------------------------------------------------- */
+
+/* One FMG cycle (Sec. 3.2) from the current solution. */
+int afg_fmg(afg_tree *t, const afg_mg_opts *opts, afg_stats *stats);
+/* One FAS V-cycle (Sec. 3.2) from the finest level. */
+int afg_vcycle(afg_tree *t, const afg_mg_opts *opts, afg_stats *stats);
+/* FMG, then V-cycles until rel_tol (or max_cycles: AFG_ERR_NOT_CONVERGED).
+ * opts->precision selects the plain FP64 method or the mixed-precision
+ * defect correction (FP64 residual and update, FP32 multigrid). */
+int afg_solve(afg_tree *t, const afg_mg_opts *opts, afg_stats *stats);
+/* max over leaves of |rho - A u| (composite operator) and of |rho|. */
+int afg_residual_norm(afg_tree *t, double *max_abs_r, double *max_abs_rho);
+
+/* Adjoint of the solve: given g = dL/du on leaf cells, solve K^T lambda = g
+ * for the transposed composite operator (FP64) and return lambda = dL/drho
+ * (leaf cells) and dL/db = -(2/h^2) lambda at the boundary-adjacent cell of
+ * every leaf boundary face.  Output pointers may be NULL. */
+int afg_adjoint(afg_tree *t, const double *g_leaf_dev, double *lambda_leaf_dev,
+                double *dL_db_face_dev, const afg_mg_opts *opts, afg_stats *stats);
+
+/* ---- batched forest ------------------------------------------------------- */
+
+/* A forest solves n independent trees together: per-level box lists are
+ * concatenated over the trees and every kernel launch covers all of them.
+ * The trees must share dim and box_n; they are copied (later changes to a
+ * tree do not affect the forest).  Field data is given per forest in
+ * canonical order, tree after tree. */
+int afg_forest_create(int n, afg_tree *const *trees, afg_forest **out);
+int afg_forest_destroy(afg_forest *f);
+int afg_forest_set_stream(afg_forest *f, void *cuda_stream);
+int afg_forest_counts(const afg_forest *f, long long *leaf_cells_per_tree, long long *bfaces_per_tree);
+int afg_forest_set_rhs(afg_forest *f, const double *rho_dev);
+int afg_forest_set_dirichlet(afg_forest *f, const double *b_dev);
+int afg_forest_get_solution(const afg_forest *f, double *u_dev);
+/* Solve every tree to opts->rel_tol; a converged tree is masked out of
+ * later cycles.  per_tree (may be NULL) receives n stats records. */
+int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+
+/* Total number of this library's kernels launched so far in this process,
+ * kernels replayed inside CUDA graphs included. */
+int afg_kernel_launches(unsigned long long *count);
+
+/* Times one kernel of the solve on its own, with CUDA events on the tree's
+ * stream: `reps` launches on every box of `level` (after one warm-up launch),
+ * in FP64 (fp64 = 1) or FP32.  kernel: 0 = red-black half-sweep (Sec. 3.1,
+ * colours alternating), 1 = fused residual + restriction (level >= 2),
+ * 2 = prolongation + correction (level >= 2), 3 = leaf residual with its
+ * max-norm reduction (all leaves; `level` ignored), 4 = FP64 FMA issue-rate
+ * probe (independent FMA chains; `level` ignored; flops count an FMA as 2;
+ * the denominator of the FP64 roofline).  Returns the mean time
+ * per launch, the cells covered (`cells`) and the algorithmic bytes and
+ * flops of one launch.  With s = 8 (FP64) or 4 (FP32) bytes per value, per
+ * cell covered: half-sweep 3s/2 bytes (other colour of u, own colour of rho
+ * and u written) and (2D+2)/2 flops; residual + restriction 2s + 3s/2^D
+ * bytes and 2D+5 flops; correction 2s + 2s/2^D bytes and 5 flops; leaf
+ * residual 2s + 4 bytes (the FP32 copy of r) and 2D+3 flops.  Field contents
+ * are overwritten.  Needs afg_set_rhs first. */
+int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
+                    double *flops, long long *cells);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,320 @@
+"""Python binding of libafgpu (``include/afgpu.h``): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; torch supplies
+device memory and the current stream.  There is no fallback: if the
+compiled library is missing, importing the binding raises.
+
+Method: Teunissen & Ebert, "Afivo" (arXiv:1701.04329): quadtree/octree AMR
+(Sec. 2), FAS multigrid with red-black Gauss-Seidel (Sec. 3).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AFG_OK, AFG_ERR_ARG, AFG_ERR_CUDA, AFG_ERR_NOMEM, AFG_ERR_STATE, AFG_ERR_NOT_CONVERGED, AFG_ERR_TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6)
+AFG_FP64, AFG_MIXED = 0, 1
+
+
+class AfgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("afgpu error %d: %s" % (code, msg))
+        self.code = code
+
+
+class MgOpts(ctypes.Structure):
+    _fields_ = [("n_down", ctypes.c_int), ("n_up", ctypes.c_int), ("n_base", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("rel_tol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("inner_vcycles", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("rel_residual", ctypes.c_double), ("max_residual", ctypes.c_double),
+                ("max_rho", ctypes.c_double), ("seconds", ctypes.c_double), ("history", ctypes.c_double * 64)]
+
+    def as_dict(self):
+        n = min(self.cycles, 64)
+        return dict(cycles=self.cycles, rel_residual=self.rel_residual, max_residual=self.max_residual,
+                    max_rho=self.max_rho, seconds=self.seconds, history=list(self.history[:max(n, 1)]))
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("box_n", ctypes.c_int), ("max_level", ctypes.c_int),
+                ("highest_level", ctypes.c_int), ("n_boxes", ctypes.c_int), ("n_leaves", ctypes.c_int),
+                ("n_leaf_cells", ctypes.c_longlong), ("n_bfaces", ctypes.c_longlong),
+                ("boxes_per_level", ctypes.c_int * 32), ("leaves_per_level", ctypes.c_int * 32)]
+
+
+_LIB = None
+P, I, LL, DBL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+_SIGS = {
+    "afg_default_opts": (None, [P]), "afg_last_error": (ctypes.c_char_p, []),
+    "afg_tree_create": (I, [I, I, I, P]), "afg_tree_destroy": (I, [P]), "afg_set_stream": (I, [P, P]),
+    "afg_refine_uniform": (I, [P, I]), "afg_cell_centers": (I, [P, P]), "afg_face_centers": (I, [P, P]),
+    "afg_leaf_levels": (I, [P, P]), "afg_adapt": (I, [P, P, I, P, P]), "afg_info": (I, [P, P]),
+    "afg_export_tree": (I, [P, P, P, P, P, P]), "afg_set_rhs": (I, [P, P]), "afg_set_dirichlet": (I, [P, P]),
+    "afg_set_solution": (I, [P, P]), "afg_get_solution": (I, [P, P]), "afg_fmg": (I, [P, P, P]),
+    "afg_vcycle": (I, [P, P, P]), "afg_solve": (I, [P, P, P]), "afg_residual_norm": (I, [P, P, P]),
+    "afg_adjoint": (I, [P, P, P, P, P, P]), "afg_forest_create": (I, [I, P, P]), "afg_forest_destroy": (I, [P]),
+    "afg_forest_set_stream": (I, [P, P]), "afg_forest_counts": (I, [P, P, P]), "afg_forest_set_rhs": (I, [P, P]),
+    "afg_forest_set_dirichlet": (I, [P, P]), "afg_forest_get_solution": (I, [P, P]),
+    "afg_forest_solve": (I, [P, P, P]), "afg_kernel_launches": (I, [P]),
+    "afg_time_kernel": (I, [P, I, I, I, I, P, P, P, P]),
+}
+
+
+def kernel_launches():
+    c = ctypes.c_ulonglong(0)
+    _check(lib().afg_kernel_launches(ctypes.byref(c)))
+    return c.value
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=True):
+    """Load libafgpu (compiling it first if sources changed and nvcc exists)."""
+    global _LIB
+    if _LIB is None:
+        if build_if_missing:
+            try:
+                _build.build()
+            except RuntimeError:
+                if not os.path.exists(_build.LIB):
+                    raise
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libafgpu.so is not built (%s); run paper_1701_04329_gb300/build.py" % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, allow=()):
+    if rc != AFG_OK and rc not in allow:
+        raise AfgError(rc, lib().afg_last_error().decode())
+    return rc
+
+
+def default_opts(**kw):
+    o = MgOpts()
+    lib().afg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown option %s" % k)
+        setattr(o, k, v)
+    return o
+
+
+def _np(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(P)
+
+
+def _dev(t, n=None):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d values, got %d" % (n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Tree:
+    """A quadtree (dim=2) or octree (dim=3) on [0,1]^dim, root box of box_n^dim
+    cells (Sec. 2.1-2.2), with its multigrid data on the GPU."""
+
+    def __init__(self, dim, box_n, max_level):
+        self.D, self.N, self.max_level = dim, box_n, max_level
+        h = ctypes.c_void_p()
+        _check(lib().afg_tree_create(dim, box_n, max_level, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and _LIB is not None:
+            _LIB.afg_tree_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    # ---- tree (host) ----------------------------------------------------------
+    def refine_uniform(self, level):
+        _check(lib().afg_refine_uniform(self._h, level))
+
+    def info(self):
+        i = TreeInfo()
+        _check(lib().afg_info(self._h, ctypes.byref(i)))
+        return i
+
+    @property
+    def n_leaf_cells(self):
+        return self.info().n_leaf_cells
+
+    @property
+    def n_bfaces(self):
+        return self.info().n_bfaces
+
+    def cell_centers(self):
+        x = np.zeros((self.n_leaf_cells, self.D))
+        _check(lib().afg_cell_centers(self._h, x.ctypes.data_as(P)))
+        return x
+
+    def face_centers(self):
+        x = np.zeros((self.n_bfaces, self.D))
+        _check(lib().afg_face_centers(self._h, x.ctypes.data_as(P)))
+        return x
+
+    def leaf_levels(self):
+        out = np.zeros(self.info().n_leaves, np.int32)
+        _check(lib().afg_leaf_levels(self._h, out.ctypes.data_as(P)))
+        return out
+
+    def adapt(self, flags, n_buf=2):
+        f, fp = _np(flags, np.int8)
+        if f.size != self.n_leaf_cells:
+            raise ValueError("need one flag per leaf cell")
+        a, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().afg_adapt(self._h, fp, n_buf, ctypes.byref(a), ctypes.byref(r)))
+        return a.value, r.value
+
+    def export(self):
+        info = self.info()
+        n, D = info.n_boxes, self.D
+        level = np.zeros(n, np.int32)
+        idx = np.zeros((n, D), np.int32)
+        parent = np.zeros(n, np.int32)
+        children = np.zeros((n, 2 ** D), np.int32)
+        nbs = np.zeros((n, 3 ** D - 1), np.int32)
+        _check(lib().afg_export_tree(self._h, *(a.ctypes.data_as(P) for a in (level, idx, parent, children, nbs))))
+        return dict(level=level, idx=idx, parent=parent, children=children, neighbours=nbs)
+
+    # ---- fields (device) -----------------------------------------------------
+    def _sync_stream(self):
+        _check(lib().afg_set_stream(self._h, _stream_ptr()))
+
+    def set_rhs(self, rho):
+        self._sync_stream()
+        _check(lib().afg_set_rhs(self._h, _dev(rho, self.n_leaf_cells)))
+
+    def set_dirichlet(self, b):
+        self._sync_stream()
+        _check(lib().afg_set_dirichlet(self._h, _dev(b, self.n_bfaces)))
+
+    def set_solution(self, u):
+        self._sync_stream()
+        _check(lib().afg_set_solution(self._h, _dev(u, self.n_leaf_cells)))
+
+    def get_solution(self, out=None):
+        import torch
+        self._sync_stream()
+        if out is None:
+            out = torch.empty(self.n_leaf_cells, dtype=torch.float64, device="cuda")
+        _check(lib().afg_get_solution(self._h, _dev(out, self.n_leaf_cells)))
+        return out
+
+    def fmg(self, opts=None):
+        self._sync_stream()
+        st = Stats()
+        _check(lib().afg_fmg(self._h, ctypes.byref(opts or default_opts()), ctypes.byref(st)))
+        return st.as_dict()
+
+    def vcycle(self, opts=None):
+        self._sync_stream()
+        st = Stats()
+        _check(lib().afg_vcycle(self._h, ctypes.byref(opts or default_opts()), ctypes.byref(st)))
+        return st.as_dict()
+
+    def solve(self, opts=None, allow_not_converged=False):
+        self._sync_stream()
+        st = Stats()
+        allow = (AFG_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(lib().afg_solve(self._h, ctypes.byref(opts or default_opts()), ctypes.byref(st)), allow)
+        return st.as_dict()
+
+    def residual_norm(self):
+        self._sync_stream()
+        r, p = ctypes.c_double(), ctypes.c_double()
+        _check(lib().afg_residual_norm(self._h, ctypes.byref(r), ctypes.byref(p)))
+        return r.value, p.value
+
+    def time_kernel(self, kernel, level, fp64=True, reps=20):
+        """Mean duration (ms) of one kernel launch plus its algorithmic bytes,
+        flops and cells (see afg_time_kernel)."""
+        self._sync_stream()
+        ms, by, fl, nc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        _check(lib().afg_time_kernel(self._h, kernel, level, int(fp64), reps, ctypes.byref(ms), ctypes.byref(by),
+                                     ctypes.byref(fl), ctypes.byref(nc)))
+        return dict(ms=ms.value, bytes=by.value, flops=fl.value, cells=nc.value)
+
+    def adjoint(self, g, opts=None):
+        """Solve K^T lam = g; returns (lam = dL/drho, dL/db) as CUDA tensors."""
+        import torch
+        self._sync_stream()
+        lam = torch.empty(self.n_leaf_cells, dtype=torch.float64, device="cuda")
+        db = torch.empty(max(self.n_bfaces, 1), dtype=torch.float64, device="cuda")
+        st = Stats()
+        _check(lib().afg_adjoint(self._h, _dev(g, self.n_leaf_cells), _dev(lam), _dev(db),
+                                 ctypes.byref(opts or default_opts()), ctypes.byref(st)))
+        return lam, db[: self.n_bfaces], st.as_dict()
+
+
+class Forest:
+    """Independent trees solved together (per-level box lists concatenated)."""
+
+    def __init__(self, trees):
+        arr = (ctypes.c_void_p * len(trees))(*[t._h.value for t in trees])
+        h = ctypes.c_void_p()
+        _check(lib().afg_forest_create(len(trees), arr, ctypes.byref(h)))
+        self._h = h
+        self.T = len(trees)
+        self.cells = np.zeros(self.T, np.int64)
+        self.faces = np.zeros(self.T, np.int64)
+        _check(lib().afg_forest_counts(self._h, self.cells.ctypes.data_as(P), self.faces.ctypes.data_as(P)))
+
+    def close(self):
+        if getattr(self, "_h", None) and _LIB is not None:
+            _LIB.afg_forest_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _sync_stream(self):
+        _check(lib().afg_forest_set_stream(self._h, _stream_ptr()))
+
+    def set_rhs(self, rho):
+        self._sync_stream()
+        _check(lib().afg_forest_set_rhs(self._h, _dev(rho, int(self.cells.sum()))))
+
+    def set_dirichlet(self, b):
+        self._sync_stream()
+        _check(lib().afg_forest_set_dirichlet(self._h, _dev(b, int(self.faces.sum()))))
+
+    def get_solution(self, out=None):
+        import torch
+        self._sync_stream()
+        if out is None:
+            out = torch.empty(int(self.cells.sum()), dtype=torch.float64, device="cuda")
+        _check(lib().afg_forest_get_solution(self._h, _dev(out, int(self.cells.sum()))))
+        return out
+
+    def solve(self, opts=None, allow_not_converged=False):
+        self._sync_stream()
+        st = (Stats * self.T)()
+        allow = (AFG_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(lib().afg_forest_solve(self._h, ctypes.byref(opts or default_opts()), st), allow)
+        return [s.as_dict() for s in st]

@@ -1,0 +1,309 @@
+// Grid construction (device metadata for a forest of trees) and the
+// multigrid drivers of arXiv:1701.04329 Sec. 3.2 on top of the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "grid.h"
+
+namespace afg {
+
+void check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        throw NoMem(std::string(what) + ": out of device memory");
+    }
+    throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+DevBuf::DevBuf(size_t n) : bytes(n) {
+    if (n == 0) return;
+    check(cudaMalloc(&p, n), "cudaMalloc");
+}
+
+DevBuf::~DevBuf() {
+    if (p) cudaFree(p);
+}
+
+namespace {
+template <typename T>
+T *upload(const std::vector<T> &v, std::vector<std::unique_ptr<DevBuf>> &owned) {
+    owned.emplace_back(new DevBuf(std::max<size_t>(1, v.size()) * sizeof(T)));
+    if (!v.empty()) check(cudaMemcpy(owned.back()->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+    return owned.back()->as<T>();
+}
+}  // namespace
+
+Grid::Grid(const std::vector<const HostTree *> &trees) {
+    D = trees[0]->D;
+    N = trees[0]->N;
+    T = (int)trees.size();
+    int nsub = 0;
+    for (int m = N / 2; m >= 2; m /= 2) ++nsub;
+    lmin = 1 - nsub;
+    lmax = 1;
+    tree_top.resize(T);
+    for (int t = 0; t < T; ++t) {
+        tree_top[t] = trees[t]->L;
+        lmax = std::max(lmax, trees[t]->L);
+        tree_cells.push_back(trees[t]->n_leaf_cells);
+        tree_faces.push_back(trees[t]->n_bfaces);
+    }
+    // global box ids: level-major, then tree, then the tree's canonical order
+    std::vector<std::vector<int>> gid(T), sub(T, std::vector<int>(nsub, -1));
+    for (int t = 0; t < T; ++t) gid[t].assign(trees[t]->boxes.size(), -1);
+    int next = 0;
+    long long cells = 0;
+    for (int l = lmin; l <= lmax; ++l) {
+        Level v{};
+        v.l = l;
+        v.M = l <= 0 ? (N >> (1 - l)) : N;
+        v.MP = l == lmin ? 0 : (l <= 1 ? v.M / 2 : N);
+        v.h = 1.0 / std::ldexp((double)N, l - 1);
+        v.b0 = next;
+        v.c0 = cells;
+        for (int t = 0; t < T; ++t) {
+            if (l <= 0) { sub[t][l - lmin] = next++; continue; }
+            const HostTree &ht = *trees[t];
+            if (l > ht.L) continue;
+            for (int b = ht.lstart[l]; b < ht.lstart[l] + ht.lcount[l]; ++b) gid[t][b] = next++;
+        }
+        v.nb = next - v.b0;
+        const long long cpb = D == 2 ? (long long)v.M * v.M : (long long)v.M * v.M * v.M;
+        v.ncell = cpb * v.nb;
+        cells += v.ncell;
+        lv.push_back(v);
+    }
+    nbox = next;
+    ncell = cells;
+    const int S = 2 * D, NC = 1 << D;
+    std::vector<int> nb(nbox * S, -1), parent(nbox, -1), poff(nbox, 0), tree(nbox, 0), child(nbox * NC, -1);
+    std::vector<long long> coff(nbox, 0);
+    std::vector<unsigned char> bflag(nbox, 0);
+    std::vector<double> hb(nbox, 0.0);
+    for (auto &v : lv) {
+        const long long cpb = v.ncell / std::max(1, v.nb);
+        for (int i = 0; i < v.nb; ++i) {
+            coff[v.b0 + i] = v.c0 + i * cpb;
+            hb[v.b0 + i] = v.h;
+        }
+    }
+    for (int t = 0; t < T; ++t) {
+        const HostTree &ht = *trees[t];
+        for (int i = 0; i < nsub; ++i) {
+            const int g = sub[t][i];
+            parent[g] = i > 0 ? sub[t][i - 1] : -1;
+            bflag[g] = BF_REFINED | BF_SPECIAL;
+            tree[g] = t;
+            child[g * NC] = i + 1 < nsub ? sub[t][i + 1] : gid[t][0];
+        }
+        for (int b = 0; b < (int)ht.boxes.size(); ++b) {
+            const HBox &hx = ht.boxes[b];
+            const int g = gid[t][b];
+            tree[g] = t;
+            if (hx.level == 1) {
+                parent[g] = sub[t][nsub - 1];
+            } else {
+                parent[g] = gid[t][hx.parent];
+                int p = 0;
+                for (int a = 0; a < D; ++a) p |= (((hx.idx[a] - 1) & 1) * (N / 2)) << (8 * a);
+                poff[g] = p;
+            }
+            bool special = false;
+            for (int s = 0; s < S; ++s) {
+                const int q = hx.nb[ht.side_dir(s)];
+                if (q >= 0) nb[g * S + s] = gid[t][q];
+                else if (q == -2) { nb[g * S + s] = -1; special = true; }
+                else {
+                    const int cq = ht.boxes[hx.parent].nb[ht.side_dir(s)];
+                    if (cq < 0) throw std::runtime_error("tree is not 2:1 balanced");
+                    nb[g * S + s] = -2 - gid[t][cq];
+                    special = true;
+                }
+            }
+            bflag[g] = (hx.leaf() ? 0 : BF_REFINED) | (special ? BF_SPECIAL : 0);
+            for (int c = 0; c < NC; ++c) child[g * NC + c] = hx.child[c] >= 0 ? gid[t][hx.child[c]] : -1;
+        }
+    }
+    // Dirichlet storage: leaf faces first, in canonical (tree-major) order, so
+    // that user face arrays map onto it directly; then the coarse boxes' faces.
+    std::vector<int> bcoff(nbox * S, -1), leaves;
+    long long off = 0;
+    for (int t = 0; t < T; ++t)
+        for (int b : trees[t]->leaves) leaves.push_back(gid[t][b]);
+    n_leaf_boxes = (int)leaves.size();
+    const int F = D == 2 ? N : N * N;
+    for (int g : leaves)
+        for (int s = 0; s < S; ++s)
+            if (nb[g * S + s] == -1) { bcoff[g * S + s] = (int)off; off += F; }
+    n_bfaces = off;
+    for (auto &v : lv) {
+        const int Fl = D == 2 ? v.M : v.M * v.M;
+        for (int g = v.b0; g < v.b0 + v.nb; ++g) {
+            if (!(bflag[g] & BF_REFINED)) continue;
+            for (int s = 0; s < S; ++s)
+                if (nb[g * S + s] == -1) { bcoff[g * S + s] = (int)off; off += Fl; }
+        }
+    }
+    nbc = off;
+    n_leaf_cells = (long long)n_leaf_boxes * (D == 2 ? N * N : N * N * N);
+
+    auto &own = owned;
+    meta.nb = upload(nb, own);
+    meta.parent = upload(parent, own);
+    meta.poff = upload(poff, own);
+    meta.coff = upload(coff, own);
+    meta.bcoff = upload(bcoff, own);
+    meta.bflag = upload(bflag, own);
+    meta.tree = upload(tree, own);
+    meta.hb = d_hb = upload(hb, own);
+    meta.active = nullptr;
+    d_child = upload(child, own);
+    d_leaves = upload(leaves, own);
+    own.emplace_back(new DevBuf(std::max<long long>(1, nbc) * sizeof(double)));
+    d_bc = own.back()->as<double>();
+    check(cudaMemset(d_bc, 0, std::max<long long>(1, nbc) * sizeof(double)), "memset bc");
+    meta.bc = d_bc;
+    // FMG masks (tree active on FMG step l iff it reaches level l) + convergence mask
+    std::vector<int> masks((size_t)(lmax - lmin + 2) * T, 1);
+    for (int l = lmin; l <= lmax; ++l)
+        for (int t = 0; t < T; ++t) masks[(size_t)(l - lmin) * T + t] = tree_top[t] >= l;
+    d_masks = upload(masks, own);
+    own.emplace_back(new DevBuf(2 * T * sizeof(unsigned long long)));
+    d_norms = own.back()->as<unsigned long long>();
+    own.emplace_back(new DevBuf(sizeof(int)));
+    d_nactive = own.back()->as<int>();
+    own.emplace_back(new DevBuf(kPartials * sizeof(double)));
+    d_partials = own.back()->as<double>();
+    own.emplace_back(new DevBuf(sizeof(double)));
+    d_scalar = own.back()->as<double>();
+    check(cudaMallocHost((void **)&h_norms, 2 * T * sizeof(unsigned long long)), "cudaMallocHost");
+    check(cudaMallocHost((void **)&h_nactive, sizeof(int)), "cudaMallocHost");
+    check(cudaMallocHost((void **)&h_scalar, sizeof(double)), "cudaMallocHost");
+    alloc_ws(ws64, true);
+}
+
+Grid::~Grid() {
+    clear_graphs();
+    if (h_norms) cudaFreeHost(h_norms);
+    if (h_nactive) cudaFreeHost(h_nactive);
+    if (h_scalar) cudaFreeHost(h_scalar);
+}
+
+void Grid::clear_graphs() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+}
+
+void Grid::alloc_ws(Workspace &w, bool fp64) {
+    const size_t bytes = (size_t)ncell * (fp64 ? 8 : 4);
+    w.fp64 = fp64;
+    w.u.reset(new DevBuf(bytes));
+    w.rho.reset(new DevBuf(bytes));
+    w.vold.reset(new DevBuf(bytes));
+    check(cudaMemset(w.u->p, 0, bytes), "memset");
+    check(cudaMemset(w.rho->p, 0, bytes), "memset");
+    check(cudaMemset(w.vold->p, 0, bytes), "memset");
+}
+
+void Grid::ensure_mixed() {
+    if (!ws32.u) alloc_ws(ws32, false);
+}
+
+void Grid::ensure_adjoint() {
+    if (!wsadj.u) alloc_ws(wsadj, true);
+    while (bicg.size() < 10) {
+        bicg.emplace_back(new DevBuf((size_t)ncell * 8));
+        check(cudaMemset(bicg.back()->p, 0, (size_t)ncell * 8), "memset");
+    }
+}
+
+// ---- multigrid building blocks --------------------------------------------
+
+void Grid::smooth(Workspace &w, int l, int steps, int hom, const int *active, cudaStream_t s) {
+    Level &v = L(l);
+    BoxMeta A = meta;
+    A.active = active;
+    const LaunchCfg c = cfg(l, w.fp64, s);
+    for (int it = 0; it < steps; ++it)
+        for (int col = 0; col < 2; ++col)
+            launch_smooth(c, A, v.b0, v.nb, nullptr, w.u->p, w.rho->p, v.h * v.h, col, hom);
+}
+
+// Residual on level l restricted to l-1 with v_H <- I v_h, v'_H <- v_H, then
+// rho_H <- I r_h + A_H(v_H) on the refined boxes of l-1 (Eq. residual,
+// Eq. coarse-rhs); leaves of l-1 store v' too.
+void Grid::down_step(Workspace &w, int l, int hom, const int *active, cudaStream_t s) {
+    Level &v = L(l), &vc = L(l - 1);
+    BoxMeta A = meta;
+    A.active = active;
+    launch_resid_restrict(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (v.h * v.h), hom);
+    launch_fas(cfg(l - 1, w.fp64, s), A, vc.b0, vc.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (vc.h * vc.h), hom);
+}
+
+// FAS V-cycle (Sec. 3.2) from ltop down to the coarsest grid and back.
+void Grid::vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
+    for (int l = ltop; l > lmin; --l) {
+        smooth(w, l, o.n_down, hom, active, s);
+        down_step(w, l, hom, active, s);
+    }
+    smooth(w, lmin, o.n_base, hom, active, s);
+    BoxMeta A = meta;
+    A.active = active;
+    for (int l = lmin + 1; l <= ltop; ++l) {
+        Level &v = L(l);
+        launch_correct(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p);
+        smooth(w, l, o.n_up, hom, active, s);
+    }
+}
+
+// FMG cycle (Sec. 3.2): restrict the current solution down, set the coarse
+// right-hand sides, then for l = coarsest..finest: store v'_l, correct from
+// l-1 and run a V-cycle from l.  In a forest a tree leaves the loop after its
+// own finest level (masked).
+void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s) {
+    for (int l = lmax; l > lmin; --l) {
+        Level &v = L(l);
+        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, w.u->p);
+    }
+    for (int l = lmax; l > lmin; --l) down_step(w, l, hom, nullptr, s);
+    const size_t es = w.fp64 ? 8 : 4;
+    for (int l = lmin; l <= lmax; ++l) {
+        Level &v = L(l);
+        const int *active = masked ? fmg_mask(l) : nullptr;
+        check(cudaMemcpyAsync((char *)w.vold->p + v.c0 * es, (char *)w.u->p + v.c0 * es, v.ncell * es,
+                              cudaMemcpyDeviceToDevice, s), "copy v'");
+        if (l > lmin) {
+            BoxMeta A = meta;
+            A.active = active;
+            launch_correct(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p);
+        }
+        vcycle(w, l, o, hom, active, s);
+    }
+}
+
+// u restricted to every parent (levels lmax..2), so that leaves next to a
+// refined same-level box see the mean of the fine cells.
+void Grid::restrict_all(Workspace &w, cudaStream_t s) {
+    for (int l = lmax; l >= 2; --l) {
+        Level &v = L(l);
+        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, w.u->p);
+    }
+}
+
+void Grid::norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s) {
+    restrict_all(w, s);
+    check(cudaMemsetAsync(d_norms, 0, 2 * T * sizeof(unsigned long long), s), "memset norms");
+    launch_leaf_residual(leaf_cfg(w.fp64, s), meta, d_leaves, n_leaf_boxes, w.u->p, w.rho->p, hom, d_norms,
+                         d_norms + T, rout, rout_f32);
+    check(cudaMemcpyAsync(h_norms, d_norms, 2 * T * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+          "norms to host");
+}
+
+void Grid::mask_update_async(double tol, cudaStream_t s) {
+    launch_mask_update(s, d_norms, T, tol, d_converged_mask(), d_nactive);
+    check(cudaMemcpyAsync(h_nactive, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s), "nactive");
+}
+
+}  // namespace afg

@@ -1,0 +1,113 @@
+// Device-resident multigrid hierarchy for one or more trees (a forest):
+// box metadata, per-level box ranges and leaf lists, field workspaces, and
+// the multigrid drivers (arXiv:1701.04329 Sec. 3.2) built on the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "host_tree.h"
+#include "launch.h"
+
+namespace afg {
+
+struct CudaError : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+struct NoMem : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+
+void check(cudaError_t e, const char *what);
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t n);
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct Workspace {
+    bool fp64 = true;
+    std::unique_ptr<DevBuf> u, rho, vold;
+};
+
+struct MgOpts {
+    int n_down = 2, n_up = 2, n_base = 4;
+};
+
+class Grid {
+  public:
+    explicit Grid(const std::vector<const HostTree *> &trees);
+    ~Grid();
+
+    struct Level {
+        int l, M, MP, b0, nb;  // MP = parent box size (0 at the bottom)
+        double h;
+        int *d_leaves = nullptr;
+        int nleaves = 0;
+        long long c0 = 0, ncell = 0;  // cell range of the level
+    };
+
+    int D, N, T, lmin, lmax;
+    std::vector<Level> lv;
+    Level &L(int l) { return lv[l - lmin]; }
+    int nbox = 0, n_leaf_boxes = 0;
+    long long ncell = 0, n_leaf_cells = 0, n_bfaces = 0, nbc = 0;
+    std::vector<long long> tree_cells, tree_faces;  // per tree
+    std::vector<int> tree_top;                      // finest level per tree
+
+    BoxMeta meta{};  // active = nullptr
+    int *d_leaves = nullptr;  // all leaf boxes, canonical (tree-major) order
+    int *d_child = nullptr;
+    double *d_hb = nullptr;
+    double *d_bc = nullptr;
+    int *d_masks = nullptr;   // row r: active[tree] for FMG level lmin + r; last row: not converged
+    int *d_converged_mask() const { return d_masks + (size_t)(lmax - lmin + 1) * T; }
+    int *fmg_mask(int l) const { return d_masks + (size_t)(l - lmin) * T; }
+    unsigned long long *d_norms = nullptr;  // 2*T: rmax[T], pmax[T]
+    unsigned long long *h_norms = nullptr;  // pinned copy
+    int *d_nactive = nullptr, *h_nactive = nullptr;
+    double *d_partials = nullptr, *d_scalar = nullptr, *h_scalar = nullptr;
+
+    std::vector<std::unique_ptr<DevBuf>> owned;  // metadata buffers
+    Workspace ws64, ws32, wsadj;
+    std::vector<std::unique_ptr<DevBuf>> bicg;  // adjoint vectors
+    bool rhs_set = false;
+
+    LaunchCfg cfg(int l, bool fp64, cudaStream_t s) {
+        auto &v = L(l);
+        return LaunchCfg{s, D, v.M, v.MP, fp64};
+    }
+    LaunchCfg leaf_cfg(bool fp64, cudaStream_t s) const { return LaunchCfg{s, D, N, N / 2, fp64}; }
+
+    void alloc_ws(Workspace &w, bool fp64);
+    void ensure_mixed();
+    void ensure_adjoint();
+
+    // ---- multigrid building blocks ---------------------------------------
+    void smooth(Workspace &w, int l, int steps, int hom, const int *active, cudaStream_t s);
+    void down_step(Workspace &w, int l, int hom, const int *active, cudaStream_t s);
+    void vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s);
+    void fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s);
+    void restrict_all(Workspace &w, cudaStream_t s);
+    // composite residual of ws64 (restriction + leaf residual), norms to host buffer (async)
+    void norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s);
+    void mask_update_async(double tol, cudaStream_t s);
+
+    // graphs keyed by a small tuple
+    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int, int, int>, int> graph_kernels;  // kernel nodes per graph
+    void clear_graphs();
+};
+
+}  // namespace afg

@@ -1,0 +1,66 @@
+// Host-side launch interface of the multigrid kernels.  Every function
+// enqueues one kernel on cfg.stream; grids are sized from the kernel's
+// occupancy times the SM count (a persistent grid looping over boxes).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace afg {
+
+struct LaunchCfg {
+    cudaStream_t stream;
+    int D;      // 2 or 3
+    int M;      // cells per box side on this level
+    int MP;     // cells per box side on the parent level (M or M/2)
+    bool fp64;  // double (true) or float (false) field data
+};
+
+// counts launches of this library's kernels (host side)
+extern unsigned long long g_launches;
+
+void launch_smooth(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u, const void *rho,
+                   double h2, int colour, int hom);
+void launch_resid_restrict(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, void *rho, void *vold,
+                           double ih2, int hom);
+void launch_fas(const LaunchCfg &, const BoxMeta &, int b0, int n, const void *u, void *rho, void *vold, double ih2,
+                int hom);
+void launch_correct(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, const void *vold);
+void launch_restrict_u(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u);
+// residual rho - A u on leaf boxes (cell size from the box metadata); the
+// residual is also stored into rout (float* when rout_f32, else double*) if
+// rout is not null
+void launch_leaf_residual(const LaunchCfg &, const BoxMeta &, const int *list, int n, const void *u, const void *rho,
+                          int hom, unsigned long long *rmax, unsigned long long *pmax, void *rout,
+                          bool rout_f32);
+// canonical leaf data <-> box storage
+void launch_leaf_set(const LaunchCfg &, const BoxMeta &, const int *list, int n, const double *src, void *dst);
+void launch_leaf_get(const LaunchCfg &, const BoxMeta &, const int *list, int n, const void *src, double *dst);
+// Dirichlet data of the boxes of a level -> their parents (face means)
+void launch_bc_restrict(const LaunchCfg &, const BoxMeta &, int b0, int n, double *bc);
+// FP64 FMA throughput probe; returns the flops of one launch (FMA = 2)
+double launch_fp64_probe(cudaStream_t s, double *scratch, int iters);
+void launch_mask_update(cudaStream_t s, const unsigned long long *norms, int T, double tol, int *active,
+                        int *nactive);
+// x (double) += e (float) on leaf boxes
+void launch_mixed_update(const LaunchCfg &, const BoxMeta &, const int *list, int n, double *x, const float *e);
+// adjoint: out = K^T lam on leaf boxes (double); hb = cell size per box
+void launch_adjoint_apply(const LaunchCfg &, const BoxMeta &, const int *child, const double *hb, const int *list,
+                          int n, const double *lam, double *out);
+// dL/db on leaf boundary faces: -(2/h^2) lam of the adjacent cell
+void launch_adjoint_db(const LaunchCfg &, const BoxMeta &, const double *hb, const int *list, int n,
+                       const double *lam, double *db);
+// leaf vectors (double): out = a x + b y + c z (y, z may be null)
+void launch_leaf_axpbypcz(const LaunchCfg &, const BoxMeta &, const int *list, int n, double *out, double a,
+                          const double *x, double b, const double *y, double c, const double *z);
+// out = x * h^(D*power) per box (power = +1 or -1)
+void launch_leaf_scale(const LaunchCfg &, const BoxMeta &, const double *hb, const int *list, int n, double *out,
+                       const double *x, int power);
+// dot product / max norm over leaf cells into *result (device), deterministic
+void launch_leaf_dot(const LaunchCfg &, const BoxMeta &, const int *list, int n, const double *x, const double *y,
+                     double *partials, double *result);
+void launch_leaf_absmax(const LaunchCfg &, const BoxMeta &, const int *list, int n, const double *x,
+                        double *partials, double *result);
+constexpr int kPartials = 4096;  // size of the partials buffer (doubles)
+
+}  // namespace afg

@@ -1,0 +1,5 @@
+// 3D instantiations of the launch layer.
+#include "launch_impl.cuh"
+namespace afg {
+template struct DimOps<3>;
+}

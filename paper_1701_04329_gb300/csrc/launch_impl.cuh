@@ -1,0 +1,274 @@
+// Template side of the launch layer; instantiated per dimension in
+// launch_d2.cu / launch_d3.cu so the two compile in parallel.
+#pragma once
+#include <algorithm>
+#include <stdexcept>
+#include <string>
+
+#include "kernels_leaf.cuh"
+#include "launch.h"
+
+namespace afg {
+
+int sm_count();
+// resident CTAs per SM of a kernel for a given dynamic shared memory size (cached)
+int occupancy(const void *kernel, size_t smem);
+
+// Persistent grid: (resident CTAs per SM) x SMs, capped by the work.
+template <typename K>
+int grid_for(K kernel, size_t smem, int work_ctas) {
+    const int cap = occupancy(reinterpret_cast<const void *>(kernel), smem) * sm_count();
+    return std::max(1, std::min(work_ctas, cap));
+}
+
+template <int D, int M>
+inline int work_ctas(int nbox) { return (nbox + Geo<D, M>::BPC - 1) / Geo<D, M>::BPC; }
+
+template <int D, int M, typename T>
+void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
+               double h2, int colour, int hom) {
+    if (n <= 0) return;
+    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    auto k = k_smooth<D, M, T>;
+    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, list, (T *)u, (const T *)rho,
+                                                                          T(h2), colour, hom);
+    ++g_launches;
+}
+
+template <int D, int M, int MP, typename T>
+void do_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
+                       double ih2, int hom) {
+    if (n <= 0) return;
+    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    auto k = k_resid_restrict<D, M, MP, T>;
+    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (T *)u, (T *)rho, (T *)vold,
+                                                                          T(ih2), hom);
+    ++g_launches;
+}
+
+template <int D, int M, typename T>
+void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold, double ih2,
+            int hom) {
+    if (n <= 0) return;
+    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    auto k = k_fas<D, M, T>;
+    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (const T *)u, (T *)rho,
+                                                                          (T *)vold, T(ih2), hom);
+    ++g_launches;
+}
+
+template <int D, int M, int MP, typename T>
+void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
+    if (n <= 0) return;
+    constexpr int Q = M / 2 + 2;
+    const size_t smem = sizeof(T) * (D == 2 ? Q * Q : Q * Q * Q) * Geo<D, M>::BPC;
+    auto k = k_correct<D, M, MP, T>;
+    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (T *)u, (const T *)vold);
+    ++g_launches;
+}
+
+template <int D, int M, int MP, typename T>
+void do_restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u) {
+    if (n <= 0) return;
+    auto k = k_restrict_u<D, M, MP, T>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, b0, n, (T *)u);
+    ++g_launches;
+}
+
+template <int D, int M, typename T>
+void do_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u, const void *rho,
+                      int hom, unsigned long long *rmax, unsigned long long *pmax, void *rout,
+                      bool rout_f32) {
+    if (n <= 0) return;
+    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    if (rout_f32) {
+        auto k = k_leaf_residual<D, M, T, float>;
+        k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(
+            A, list, n, (const T *)u, (const T *)rho, hom, rmax, pmax, (float *)rout);
+    } else {
+        auto k = k_leaf_residual<D, M, T, double>;
+        k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(
+            A, list, n, (const T *)u, (const T *)rho, hom, rmax, pmax, (double *)rout);
+    }
+    ++g_launches;
+}
+
+template <int D, int M, typename T>
+void do_leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
+    if (n <= 0) return;
+    auto k = k_leaf_set<D, M, T>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, src, (T *)dst);
+    ++g_launches;
+}
+
+template <int D, int M, typename T>
+void do_leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
+    if (n <= 0) return;
+    auto k = k_leaf_get<D, M, T>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, (const T *)src, dst);
+    ++g_launches;
+}
+
+template <int D, int M, int MP>
+void do_bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc) {
+    if (n <= 0) return;
+    auto k = k_bc_restrict<D, M, MP>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, b0, n, bc);
+    ++g_launches;
+}
+
+template <int D, int M>
+void do_mixed_update(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *x, const float *e) {
+    if (n <= 0) return;
+    auto k = k_mixed_update<D, M>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, x, e);
+    ++g_launches;
+}
+
+template <int D, int M>
+void do_adjoint_apply(const LaunchCfg &c, const BoxMeta &A, const int *child, const double *hb, const int *list,
+                      int n, const double *lam, double *out) {
+    if (n <= 0) return;
+    const size_t smem = sizeof(double) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    auto k = k_adjoint_apply<D, M>;
+    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, child, hb, list, n, lam, out);
+    ++g_launches;
+}
+
+template <int D, int M>
+void do_adjoint_db(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n, const double *lam,
+                   double *db) {
+    if (n <= 0) return;
+    auto k = k_adjoint_db<D, M>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, hb, list, n, lam, db);
+    ++g_launches;
+}
+
+template <int D, int M>
+void do_axpbypcz(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *out, double a,
+                 const double *x, double b, const double *y, double cc, const double *z) {
+    if (n <= 0) return;
+    auto k = k_leaf_axpbypcz<D, M>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, out, a, x, b, y, cc, z);
+    ++g_launches;
+}
+
+template <int D, int M>
+void do_scale(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n, double *out,
+              const double *x, int power) {
+    if (n <= 0) return;
+    auto k = k_leaf_scale<D, M>;
+    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, hb, list, n, out, x, power);
+    ++g_launches;
+}
+
+template <int D, int M>
+void do_reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *x, const double *y,
+               int mode, double *partials, double *result) {
+    auto k = k_leaf_reduce<D, M>;
+    const int grid = std::min(kPartials, grid_for(k, 0, std::max(1, work_ctas<D, M>(n))));
+    k<<<grid, kThreads, 0, c.stream>>>(A, list, n, x, y, mode, partials);
+    k_reduce_final<<<1, kThreads, 0, c.stream>>>(partials, grid, mode, result);
+    g_launches += 2;
+}
+
+// ---- dispatch over the box size --------------------------------------------
+[[noreturn]] inline void bad_size(int M, int MP) {
+    throw std::runtime_error("unsupported box size " + std::to_string(M) + "/" + std::to_string(MP));
+}
+
+#define AFG_SWITCH_M(M, BODY)                       \
+    switch (M) {                                    \
+        case 2: { constexpr int MM = 2; BODY; break; }   \
+        case 4: { constexpr int MM = 4; BODY; break; }   \
+        case 8: { constexpr int MM = 8; BODY; break; }   \
+        case 16: { constexpr int MM = 16; BODY; break; } \
+        default: bad_size(M, 0);                    \
+    }
+
+// (M, MP) pairs: same size (tree levels >= 2) or half size (root and below)
+#define AFG_SWITCH_MMP(M, MP, BODY)                                                   \
+    if ((M) == (MP)) {                                                                \
+        switch (M) {                                                                  \
+            case 4: { constexpr int MM = 4, PP = 4; BODY; break; }                    \
+            case 8: { constexpr int MM = 8, PP = 8; BODY; break; }                    \
+            case 16: { constexpr int MM = 16, PP = 16; BODY; break; }                 \
+            default: bad_size(M, MP);                                                 \
+        }                                                                             \
+    } else if (2 * (MP) == (M)) {                                                     \
+        switch (M) {                                                                  \
+            case 4: { constexpr int MM = 4, PP = 2; BODY; break; }                    \
+            case 8: { constexpr int MM = 8, PP = 4; BODY; break; }                    \
+            case 16: { constexpr int MM = 16, PP = 8; BODY; break; }                  \
+            default: bad_size(M, MP);                                                 \
+        }                                                                             \
+    } else bad_size(M, MP);
+
+template <int D>
+struct DimOps {
+    static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
+                       const void *rho, double h2, int colour, int hom) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_smooth<D, MM, double>(c, A, b0, n, list, u, rho, h2, colour, hom))); }
+        else { AFG_SWITCH_M(c.M, (do_smooth<D, MM, float>(c, A, b0, n, list, u, rho, h2, colour, hom))); }
+    }
+    static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
+                               double ih2, int hom) {
+        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_resid_restrict<D, MM, PP, double>(c, A, b0, n, u, rho, vold, ih2, hom))); }
+        else { AFG_SWITCH_MMP(c.M, c.MP, (do_resid_restrict<D, MM, PP, float>(c, A, b0, n, u, rho, vold, ih2, hom))); }
+    }
+    static void fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
+                    double ih2, int hom) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_fas<D, MM, double>(c, A, b0, n, u, rho, vold, ih2, hom))); }
+        else { AFG_SWITCH_M(c.M, (do_fas<D, MM, float>(c, A, b0, n, u, rho, vold, ih2, hom))); }
+    }
+    static void correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
+        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, double>(c, A, b0, n, u, vold))); }
+        else { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, float>(c, A, b0, n, u, vold))); }
+    }
+    static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u) {
+        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, double>(c, A, b0, n, u))); }
+        else { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, float>(c, A, b0, n, u))); }
+    }
+    static void leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
+                              const void *rho, int hom, unsigned long long *rmax,
+                              unsigned long long *pmax, void *rout, bool rout_f32) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_leaf_residual<D, MM, double>(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32))); }
+        else { AFG_SWITCH_M(c.M, (do_leaf_residual<D, MM, float>(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32))); }
+    }
+    static void leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_leaf_set<D, MM, double>(c, A, list, n, src, dst))); }
+        else { AFG_SWITCH_M(c.M, (do_leaf_set<D, MM, float>(c, A, list, n, src, dst))); }
+    }
+    static void leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_leaf_get<D, MM, double>(c, A, list, n, src, dst))); }
+        else { AFG_SWITCH_M(c.M, (do_leaf_get<D, MM, float>(c, A, list, n, src, dst))); }
+    }
+    static void bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc) {
+        AFG_SWITCH_MMP(c.M, c.MP, (do_bc_restrict<D, MM, PP>(c, A, b0, n, bc)));
+    }
+    static void mixed_update(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *x, const float *e) {
+        AFG_SWITCH_M(c.M, (do_mixed_update<D, MM>(c, A, list, n, x, e)));
+    }
+    static void adjoint_apply(const LaunchCfg &c, const BoxMeta &A, const int *child, const double *hb,
+                              const int *list, int n, const double *lam, double *out) {
+        AFG_SWITCH_M(c.M, (do_adjoint_apply<D, MM>(c, A, child, hb, list, n, lam, out)));
+    }
+    static void adjoint_db(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n,
+                           const double *lam, double *db) {
+        AFG_SWITCH_M(c.M, (do_adjoint_db<D, MM>(c, A, hb, list, n, lam, db)));
+    }
+    static void axpbypcz(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *out, double a,
+                         const double *x, double b, const double *y, double cc, const double *z) {
+        AFG_SWITCH_M(c.M, (do_axpbypcz<D, MM>(c, A, list, n, out, a, x, b, y, cc, z)));
+    }
+    static void scale(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n, double *out,
+                      const double *x, int power) {
+        AFG_SWITCH_M(c.M, (do_scale<D, MM>(c, A, hb, list, n, out, x, power)));
+    }
+    static void reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *x,
+                       const double *y, int mode, double *partials, double *result) {
+        AFG_SWITCH_M(c.M, (do_reduce<D, MM>(c, A, list, n, x, y, mode, partials, result)));
+    }
+};
+
+}  // namespace afg

@@ -1,0 +1,51 @@
+"""The C-ABI library loads without a GPU and exports every symbol that
+include/afgpu.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+from paper_1701_04329_gb300 import afgpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "afgpu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(afg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = afgpu.lib()
+    names = declared_symbols()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in afgpu._SIGS, n
+
+
+def test_errors_are_status_codes():
+    L = afgpu.lib()
+    h = ctypes.c_void_p()
+    assert L.afg_tree_create(4, 8, 3, ctypes.byref(h)) == afgpu.AFG_ERR_ARG
+    assert b"dim" in L.afg_last_error()
+    assert L.afg_tree_create(2, 6, 3, ctypes.byref(h)) == afgpu.AFG_ERR_ARG
+    assert L.afg_tree_create(3, 8, 22, ctypes.byref(h)) == afgpu.AFG_ERR_ARG
+    t = afgpu.Tree(2, 8, 4)
+    try:
+        t.refine_uniform(9)
+        assert False, "expected an error"
+    except afgpu.AfgError as e:
+        assert e.code == afgpu.AFG_ERR_ARG
+    import numpy as np
+    try:
+        t.adapt(np.full(t.n_leaf_cells, 3, np.int8))
+        assert False
+    except afgpu.AfgError as e:
+        assert e.code == afgpu.AFG_ERR_ARG
+    try:
+        t.adapt(np.zeros(t.n_leaf_cells, np.int8), n_buf=9)
+        assert False
+    except afgpu.AfgError as e:
+        assert e.code == afgpu.AFG_ERR_ARG
+    assert t.info().n_boxes == 1  # failed calls left the tree unchanged

@@ -1,0 +1,54 @@
+"""The library's tree builder (host C++) against the oracle's, bit for bit:
+box order, levels, spatial indices, parent/children/neighbour ids, cell and
+face centres (arXiv:1701.04329 Sec. 2.1-2.3).  No GPU."""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleTree
+from paper_1701_04329_gb300 import afgpu
+from paper_1701_04329_gb300 import workloads as W
+from tests.treecheck import check_tree
+
+
+def same_tree(a, b):
+    ea, eb = a.export(), b.export()
+    for k in ("level", "idx", "parent", "children", "neighbours"):
+        assert np.array_equal(ea[k], eb[k]), k
+    assert np.array_equal(a.cell_centers(), b.cell_centers())
+    assert np.array_equal(a.face_centers(), b.face_centers())
+    assert np.array_equal(a.leaf_levels(), b.leaf_levels())
+    return ea
+
+
+@pytest.mark.parametrize("D,N,seed", [(2, 4, 1), (2, 8, 2), (2, 16, 3), (3, 4, 4), (3, 8, 5)])
+def test_random_adapt_sequences(D, N, seed):
+    rng = np.random.default_rng(seed)
+    maxl = 6 if D == 2 else 4
+    a, b = OracleTree(D, N, maxl), afgpu.Tree(D, N, maxl)
+    for t in (a, b):
+        t.refine_uniform(2)
+    for step in range(6):
+        n = a.n_leaf_cells
+        assert n == b.n_leaf_cells
+        lv = np.repeat(a.leaf_levels(), N ** D)
+        flags = rng.choice(np.array([-1, 0, 1], np.int8), size=n, p=[0.5, 0.45, 0.05])
+        # whole boxes flagged -1 now and then, so derefinement happens too
+        boxes = rng.random(n // N ** D) < 0.5
+        flags[np.repeat(boxes, N ** D)] = -1
+        nbuf = int(rng.integers(0, 3))
+        ra = a.adapt(flags, nbuf)
+        rb = b.adapt(flags, nbuf)
+        assert ra == rb
+        e = same_tree(a, b)
+        check_tree(e, D)
+
+
+@pytest.mark.parametrize("make", [W.gauss2d, lambda: W.twosrc3d(uniform_level=4, extra_levels=2, s=0.04),
+                                  lambda: W.forest2d_problem(W.forest2d_params(3)[2]),
+                                  lambda: W.blobs3d(uniform_level=3)])
+def test_workload_trees(make):
+    p = make()
+    a, b = OracleTree(p.dim, p.box_n, p.max_level), afgpu.Tree(p.dim, p.box_n, p.max_level)
+    p.build(a)
+    p.build(b)
+    same_tree(a, b)
