@@ -43,7 +43,28 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--uniform-level", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", choices=["smooth", "resid", "correct", "leafres"],
+                    help="time one kernel on a uniform tree of --uniform-level (profiling case)")
+    ap.add_argument("--fp32", action="store_true")
+    ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
+
+
+def kernel_only(args):
+    """One kernel on the uniform 3D tree of --uniform-level, nothing else: the
+    case the ncu captures use (level 6: 256^3 cells, fields larger than L2)."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    t = afgpu.Tree(3, 8, args.uniform_level)
+    t.refine_uniform(args.uniform_level)
+    n = t.n_leaf_cells
+    x = torch.linspace(0, 1, n, dtype=torch.float64, device="cuda")
+    t.set_rhs(torch.sin(7 * x))
+    k = {"smooth": 0, "resid": 1, "correct": 2, "leafres": 3}[args.kernel_only]
+    r = t.time_kernel(k, args.uniform_level, not args.fp32, args.reps)
+    r.update(kernel=args.kernel_only, dtype="f32" if args.fp32 else "f64", level=args.uniform_level,
+             gbs=r["bytes"] / (r["ms"] * 1e-3) / 1e9, tflops=r["flops"] / (r["ms"] * 1e-3) / 1e12)
+    print(json.dumps(r), flush=True)
 
 
 def peaks():
@@ -178,6 +199,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.kernel_only:
+        kernel_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

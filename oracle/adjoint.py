@@ -1,0 +1,78 @@
+"""FP64 adjoint of the composite solve -- TEST INFRASTRUCTURE ONLY.
+
+Not in the paper (an addition): for a loss L(u) with u = A^-1(rho, b), the
+gradient is lam = K^-T dL/du (K = the composite leaf operator, Sec. 3.2-3.3)
+and dL/db_f = -(2/h^2) lam_i(f) (Dirichlet ghost 2b - u).  K is not symmetric
+on refined trees (the conservative refinement-boundary ghosts couple fine to
+coarse with 1/2 but coarse to fine through the mean of the children), so the
+true transpose is needed.  Two solvers:
+
+* direct(): scipy sparse LU of K^T (the definition, for small trees);
+* bicgstab(): BiCGStab (van der Vorst 1992) with right preconditioner
+  W M W^-1, M = one oracle V-cycle from zero with homogeneous Dirichlet data,
+  W = diag(cell volumes) -- W K is symmetric up to the refinement-boundary
+  terms, so W M W^-1 approximates K^-T.
+"""
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from . import composite
+
+
+def direct(tree, g):
+    K = tree.leaf_rows()
+    return spla.spsolve(K.T.tocsc(), g)
+
+
+def dl_db(tree, lam):
+    e = tree.export()
+    _, B = composite.assemble(tree.D, tree.N, e["level"], e["idx"], e["children"])
+    return -(B.T @ lam)
+
+
+def bicgstab(tree, g, tol=1e-12, maxit=100, n_down=2, n_up=2, n_base=4):
+    """The tree's rhs/solution/boundary data are overwritten."""
+    KT = tree.leaf_rows().T.tocsr()
+    e = tree.export()
+    w = composite.cell_volumes(tree.D, tree.N, e["level"], e["children"])
+    tree.set_dirichlet(np.zeros(tree.n_bfaces))
+    tree.set_homogeneous(1)
+
+    def P(r):
+        tree.set_rhs(r / w)
+        tree.zero_solution()
+        tree.vcycle(n_down, n_up, n_base)
+        return w * tree.get_solution()
+
+    b = np.asarray(g, dtype=np.float64)
+    bn = np.abs(b).max()
+    x = np.zeros_like(b)
+    if bn == 0:
+        return x, 0
+    r = b.copy()
+    rh = r.copy()
+    p = np.zeros_like(b)
+    v = np.zeros_like(b)
+    rho_old = alpha = omega = 1.0
+    it = 0
+    for it in range(1, maxit + 1):
+        rho_new = rh @ r
+        beta = (rho_new / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = P(p)
+        v = KT @ ph
+        alpha = rho_new / (rh @ v)
+        s = r - alpha * v
+        if np.abs(s).max() / bn <= tol:
+            x += alpha * ph
+            break
+        sh = P(s)
+        t = KT @ sh
+        omega = (t @ s) / (t @ t)
+        x += alpha * ph + omega * sh
+        r = s - omega * t
+        if np.abs(r).max() / bn <= tol:
+            break
+        rho_old = rho_new
+    tree.set_homogeneous(0)
+    return x, it

@@ -62,6 +62,7 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
         v.MP = l == lmin ? 0 : (l <= 1 ? v.M / 2 : N);
         v.h = 1.0 / std::ldexp((double)N, l - 1);
         v.b0 = next;
+        cells = (cells + 63) / 64 * 64;  // 64-cell alignment keeps every box 16-byte aligned for vector loads
         v.c0 = cells;
         for (int t = 0; t < T; ++t) {
             if (l <= 0) { sub[t][l - lmin] = next++; continue; }
@@ -147,6 +148,15 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
         }
     }
     nbc = off;
+    // per side: the cells of the box a ghost reads from, or its Dirichlet data
+    std::vector<long long> nbase(nbox * S, 0);
+    for (int g = 0; g < nbox; ++g)
+        for (int s = 0; s < S; ++s) {
+            const int code = nb[g * S + s];
+            if (code >= 0) nbase[g * S + s] = coff[code];
+            else if (code == -1) nbase[g * S + s] = bcoff[g * S + s];
+            else nbase[g * S + s] = coff[-2 - code];
+        }
     n_leaf_cells = (long long)n_leaf_boxes * (D == 2 ? N * N : N * N * N);
 
     auto &own = owned;
@@ -158,6 +168,7 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     meta.bflag = upload(bflag, own);
     meta.tree = upload(tree, own);
     meta.hb = d_hb = upload(hb, own);
+    meta.nbase = upload(nbase, own);
     meta.active = nullptr;
     d_child = upload(child, own);
     d_leaves = upload(leaves, own);

@@ -47,7 +47,73 @@ struct BoxMeta {
     const int *active;  // may be null
     const double *bc;
     const double *hb;   // cell size of every box
+    const long long *nbase;  // per side: cells of the neighbour / coarse box, or Dirichlet data offset
 };
+
+// Metadata of one box, prefetched into shared memory one box ahead.
+struct BoxInfo {
+    long long coff;
+    long long base[6];
+    int code[6];
+    int b, flag, poff, parent;
+};
+
+// Loads the metadata of entry `idx` of a level range (b0 + idx) or list.
+// Threads lt, lt+G, ... of the box's group share the work; b = -1 marks an
+// empty slot (past the end, or a masked tree).
+template <int D>
+__device__ __forceinline__ void info_load(const BoxMeta &A, int idx, int n, int b0, const int *list, BoxInfo &I,
+                                          int lt, int G) {
+    for (int x = lt; x <= 2 * D; x += G) {
+        int b = -1;
+        if (idx < n) b = list ? list[idx] : b0 + idx;
+        if (x < 2 * D) {
+            if (b >= 0) {
+                I.code[x] = A.nb[b * 2 * D + x];
+                I.base[x] = A.nbase[b * 2 * D + x];
+            }
+        } else {
+            if (b >= 0 && A.active && !A.active[A.tree[b]]) b = -1;
+            I.b = b;
+            if (b >= 0) {
+                I.coff = A.coff[b];
+                I.flag = A.bflag[b];
+                I.poff = A.poff[b];
+                I.parent = A.parent[b];
+            }
+        }
+    }
+}
+
+template <typename T, int VEC>
+struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<float, 1> { using type = float; };
+template <> struct VecT<double, 2> { using type = double2; };
+template <> struct VecT<double, 1> { using type = double; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ void ldv(const T *__restrict__ p, T *out) {
+    using V = typename VecT<T, VEC>::type;
+    const V v = *reinterpret_cast<const V *>(p);
+    const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) out[i] = e[i];
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void stv(T *p, const T *in) {
+    using V = typename VecT<T, VEC>::type;
+    V v;
+    T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) e[i] = in[i];
+    *reinterpret_cast<V *>(p) = v;
+}
+
+template <typename T, int H>
+constexpr int vec_of() { return (16 / (int)sizeof(T)) < H ? 16 / (int)sizeof(T) : H; }
 
 template <int D, int M>
 struct Geo {
@@ -98,97 +164,110 @@ __device__ __forceinline__ void face_pos(int D, int s, int pos, int t1, int t2, 
 
 __device__ __forceinline__ int unpack_off(int p, int a) { return (p >> (8 * a)) & 0xff; }
 
-// ---------------------------------------------------------------------------
-// Ghost assembly.  Phase A (global reads only) stores the same-level ghost,
-// the Dirichlet value b (domain boundary) or the coarse value u_H
-// (refinement boundary) into the ghost slot; phase B, after a barrier,
-// turns the last two into ghost values with the box's own cells:
-//   Dirichlet:           g = 2 b - u_1
-//   refinement boundary: 2D g = u_H/2 + u_1 - (u_t + u_2)/4
-//                        3D g = u_H/2 + 5/4 u_1 - (u_2 + u_t1 + u_t2)/4
-// (Sec. 2.4 and the default scheme of Sec. 3.3).  `only` < 0: all side
-// ghosts; otherwise only ghosts next to interior cells of colour `only`.
-// ---------------------------------------------------------------------------
-template <int D, int M, typename T>
-__device__ __forceinline__ void ghosts_phase_a(const BoxMeta &A, int b, const T *__restrict__ u, T *tile,
-                                               int lt, int nthr, int only, int hom) {
-    constexpr int F = Geo<D, M>::F;
-    const int nf = only < 0 ? F : F / 2;
-    for (int s = 0; s < 2 * D; ++s) {
-        const int code = A.nb[b * 2 * D + s];
-        const int hi = s & 1, a = s >> 1;
-        const int pin = hi ? M - 1 : 0, pg = hi ? M : -1;
-        for (int f = lt; f < nf; f += nthr) {
-            int t1, t2;
-            if (only < 0) { t1 = f % M; t2 = D == 3 ? f / M : 0; }
-            else {
-                t2 = D == 3 ? f / (M / 2) : 0;
-                const int h1 = D == 3 ? f % (M / 2) : f;
-                t1 = 2 * h1 + ((only + pin + t2 + D) & 1);
-            }
-            int i, j, k;
-            face_pos(D, s, pg, t1, t2, i, j, k);
-            T v;
-            if (code >= 0) {
-                int mi, mj, mk;
-                face_pos(D, s, hi ? 0 : M - 1, t1, t2, mi, mj, mk);
-                v = u[A.coff[code] + rbi<D, M>(mi, mj, mk)];
-            } else if (code == -1) {
-                v = hom ? T(0) : T(A.bc[A.bcoff[b * 2 * D + s] + t2 * M + t1]);
-            } else {
-                const int cb = -2 - code;
-                const int po = A.poff[b];
-                int ci, cj, ck;
-                int c1 = 0, c2 = 0;
-                // tangential axes in increasing order
-                const int ta1 = a == 0 ? 1 : 0, ta2 = a == 2 ? 1 : 2;
-                c1 = unpack_off(po, ta1) + (t1 >> 1);
-                c2 = D == 3 ? unpack_off(po, ta2) + (t2 >> 1) : 0;
-                face_pos(D, s, hi ? 0 : M - 1, c1, c2, ci, cj, ck);
-                v = u[A.coff[cb] + rbi<D, M>(ci, cj, ck)];
-            }
-            tile[ti<D, M>(i, j, k)] = v;
-        }
+// face cell f of a side: all cells (only < 0) or the half whose interior
+// neighbour has colour `only` (a checkerboard of the face)
+template <int D, int M>
+__device__ __forceinline__ void face_cell(int f, int only, int pin, int &t1, int &t2) {
+    if (only < 0) {
+        t1 = f % M;
+        t2 = D == 3 ? f / M : 0;
+    } else {
+        t2 = D == 3 ? f / (M / 2) : 0;
+        const int h1 = D == 3 ? f % (M / 2) : f;
+        t1 = 2 * h1 + ((only + pin + t2 + D) & 1);
     }
 }
 
-template <int D, int M, typename T>
-__device__ __forceinline__ void ghosts_phase_b(const BoxMeta &A, int b, T *tile, int lt, int nthr, int only) {
+// ---------------------------------------------------------------------------
+// Box staging.  gather() issues every global load of a box at once: the
+// interior colour halves as 16-byte vectors, and the side ghosts of all
+// sides together -- the neighbour's face cell (same level), the Dirichlet
+// value b (domain boundary) or the coarse value u_H (refinement boundary).
+// finalize(), after a barrier, turns the last two into ghost values with
+// the box's own cells (Sec. 2.4 and the default scheme of Sec. 3.3):
+//   Dirichlet:           g = 2 b - u_1
+//   refinement boundary: 2D g = u_H/2 + u_1 - (u_t + u_2)/4
+//                        3D g = u_H/2 + 5/4 u_1 - (u_2 + u_t1 + u_t2)/4
+// `only` < 0: all side ghosts; otherwise only the ghosts next to interior
+// cells of colour `only` (all a half-sweep of that colour reads).
+// ---------------------------------------------------------------------------
+template <int D, int M, typename T, int G>
+__device__ __forceinline__ void gather(const BoxInfo &I, const T *__restrict__ u, const double *__restrict__ bc,
+                                       T *tile, int lt, int only, bool own, int hom) {
+    constexpr int C = Geo<D, M>::C, H = Geo<D, M>::H, F = Geo<D, M>::F;
+    constexpr int VEC = vec_of<T, H>();
+    const int q0 = (only < 0 || own) ? 0 : (1 - only) * H;
+    const int q1 = (only < 0 || own) ? C : (2 - only) * H;
+    for (int v = q0 / VEC + lt; v < q1 / VEC; v += G) {
+        T e[VEC];
+        ldv<T, VEC>(u + I.coff + (long long)v * VEC, e);
+#pragma unroll
+        for (int x = 0; x < VEC; ++x) {
+            int i, j, k;
+            rb_cell<D, M>(v * VEC + x, i, j, k);
+            tile[ti<D, M>(i, j, k)] = e[x];
+        }
+    }
+    const int nf = only < 0 ? F : F / 2;
+    for (int item = lt; item < 2 * D * nf; item += G) {
+        const int s = item / nf, f = item - s * nf;
+        const int code = I.code[s];
+        const long long base = I.base[s];
+        const int hi = s & 1, a = s >> 1;
+        int t1, t2;
+        face_cell<D, M>(f, only, hi ? M - 1 : 0, t1, t2);
+        int i, j, k;
+        face_pos(D, s, hi ? M : -1, t1, t2, i, j, k);
+        T v;
+        if (code >= 0) {
+            int mi, mj, mk;
+            face_pos(D, s, hi ? 0 : M - 1, t1, t2, mi, mj, mk);
+            v = u[base + rbi<D, M>(mi, mj, mk)];
+        } else if (code == -1) {
+            v = hom ? T(0) : T(bc[base + t2 * M + t1]);
+        } else {
+            const int ta1 = a == 0 ? 1 : 0, ta2 = a == 2 ? 1 : 2;
+            const int c1 = unpack_off(I.poff, ta1) + (t1 >> 1);
+            const int c2 = D == 3 ? unpack_off(I.poff, ta2) + (t2 >> 1) : 0;
+            int ci, cj, ck;
+            face_pos(D, s, hi ? 0 : M - 1, c1, c2, ci, cj, ck);
+            v = u[base + rbi<D, M>(ci, cj, ck)];
+        }
+        tile[ti<D, M>(i, j, k)] = v;
+    }
+}
+
+template <int D, int M, typename T, int G>
+__device__ __forceinline__ void finalize(const BoxInfo &I, T *tile, int lt, int only) {
     constexpr int F = Geo<D, M>::F;
     const int nf = only < 0 ? F : F / 2;
-    for (int s = 0; s < 2 * D; ++s) {
-        const int code = A.nb[b * 2 * D + s];
+    for (int item = lt; item < 2 * D * nf; item += G) {
+        const int s = item / nf, f = item - s * nf;
+        const int code = I.code[s];
         if (code >= 0) continue;
         const int hi = s & 1;
         const int pin = hi ? M - 1 : 0, pg = hi ? M : -1, p2 = hi ? M - 2 : 1;
-        for (int f = lt; f < nf; f += nthr) {
-            int t1, t2;
-            if (only < 0) { t1 = f % M; t2 = D == 3 ? f / M : 0; }
-            else {
-                t2 = D == 3 ? f / (M / 2) : 0;
-                const int h1 = D == 3 ? f % (M / 2) : f;
-                t1 = 2 * h1 + ((only + pin + t2 + D) & 1);
-            }
-            int i, j, k;
-            face_pos(D, s, pg, t1, t2, i, j, k);
-            const int gidx = ti<D, M>(i, j, k);
-            face_pos(D, s, pin, t1, t2, i, j, k);
-            const T u1 = tile[ti<D, M>(i, j, k)];
-            if (code == -1) {
-                tile[gidx] = T(2) * tile[gidx] - u1;
+        int t1, t2;
+        face_cell<D, M>(f, only, pin, t1, t2);
+        int i, j, k;
+        face_pos(D, s, pg, t1, t2, i, j, k);
+        const int gidx = ti<D, M>(i, j, k);
+        face_pos(D, s, pin, t1, t2, i, j, k);
+        const T u1 = tile[ti<D, M>(i, j, k)];
+        if (code == -1) {
+            tile[gidx] = T(2) * tile[gidx] - u1;
+        } else {
+            const T uH = tile[gidx];
+            face_pos(D, s, p2, t1, t2, i, j, k);
+            const T u2 = tile[ti<D, M>(i, j, k)];
+            face_pos(D, s, pin, t1 ^ 1, t2, i, j, k);
+            const T ut1 = tile[ti<D, M>(i, j, k)];
+            if (D == 2) {
+                tile[gidx] = T(0.5) * uH + u1 - T(0.25) * (ut1 + u2);
             } else {
-                const T uH = tile[gidx];
-                face_pos(D, s, p2, t1, t2, i, j, k);
-                const T u2 = tile[ti<D, M>(i, j, k)];
-                face_pos(D, s, pin, t1 ^ 1, t2, i, j, k);
-                const T ut1 = tile[ti<D, M>(i, j, k)];
-                if (D == 2) {
-                    tile[gidx] = T(0.5) * uH + u1 - T(0.25) * (ut1 + u2);
-                } else {
-                    face_pos(D, s, pin, t1, t2 ^ 1, i, j, k);
-                    const T ut2 = tile[ti<D, M>(i, j, k)];
-                    tile[gidx] = T(0.5) * uH + T(1.25) * u1 - T(0.25) * ((u2 + ut1) + ut2);
-                }
+                face_pos(D, s, pin, t1, t2 ^ 1, i, j, k);
+                const T ut2 = tile[ti<D, M>(i, j, k)];
+                tile[gidx] = T(0.5) * uH + T(1.25) * u1 - T(0.25) * ((u2 + ut1) + ut2);
             }
         }
     }
@@ -210,7 +289,7 @@ __device__ __forceinline__ int resolve_box(const BoxMeta &A, int idx, int n, int
     return b;
 }
 
-// load the full box (both colours) into the tile
+// load the full box (both colours) into the tile (scalar; used off the hot path)
 template <int D, int M, typename T>
 __device__ __forceinline__ void load_box(const T *__restrict__ u, long long cb, T *tile, int lt, int q0, int q1) {
     constexpr int G = Geo<D, M>::G;
@@ -221,42 +300,98 @@ __device__ __forceinline__ void load_box(const T *__restrict__ u, long long cb, 
     }
 }
 
+// vector copy of a box's C values (rb order) into shared memory
+template <int D, int M, typename T, int G>
+__device__ __forceinline__ void stage_flat(const T *__restrict__ src, T *dst, int lt) {
+    constexpr int C = Geo<D, M>::C;
+    constexpr int VEC = vec_of<T, Geo<D, M>::H>();
+    for (int v = lt; v < C / VEC; v += G) {
+        T e[VEC];
+        ldv<T, VEC>(src + (long long)v * VEC, e);
+#pragma unroll
+        for (int x = 0; x < VEC; ++x) dst[v * VEC + x] = e[x];
+    }
+}
+
+// Launch geometry of the half-sweep: one thread per 16-byte vector of a
+// colour half (capped at the CTA size).
+template <int D, int M, typename T>
+struct SmCfg {
+    static constexpr int H = Geo<D, M>::H;
+    static constexpr int VEC = vec_of<T, H>();
+    static constexpr int NV = H / VEC;
+    static constexpr int G = NV < kThreads ? NV : kThreads;
+    static constexpr int BPC = kThreads / G;
+    static constexpr int NIT = (NV + G - 1) / G;
+    static constexpr size_t smem() { return sizeof(T) * Geo<D, M>::PC * BPC + 2 * sizeof(BoxInfo) * BPC; }
+};
+
+// Launch geometry of the full-box kernels (residual, FAS): a tile plus the
+// box's rho in shared memory.
+template <int D, int M, typename T>
+struct FullCfg {
+    static constexpr int G = Geo<D, M>::G;
+    static constexpr int BPC = Geo<D, M>::BPC;
+    static constexpr size_t smem() {
+        return sizeof(T) * (Geo<D, M>::PC + Geo<D, M>::C) * BPC + 2 * sizeof(BoxInfo) * BPC;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Red-black Gauss-Seidel half-sweep on every box of a level (Sec. 3.1):
 // cells of colour `colour` get u = (sum of the 2D neighbours - h^2 rho)/(2D).
 // Cross-box reads touch only cells of the other colour, which this launch
-// never writes, so one launch per half-sweep is race free.
+// never writes, so one launch per half-sweep is race free.  Persistent CTAs
+// walk the level; each box's metadata is prefetched one box ahead.
 // ---------------------------------------------------------------------------
 template <int D, int M, typename T>
 __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, const int *list, T *u,
                                                      const T *__restrict__ rho, T h2, int colour, int hom) {
+    using S = SmCfg<D, M, T>;
     using Gm = Geo<D, M>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw) + (threadIdx.x / Gm::G) * Gm::PC;
-    const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * Gm::PC;
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * Gm::PC * S::BPC);
     const T inv = T(1) / T(2 * D);
-    for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
-        const int b = resolve_box<D, M>(A, base + g, n, b0, list);
-        bool special = false;
-        long long cb = 0;
+    const int stride = gridDim.x * S::BPC;
+    int base = blockIdx.x * S::BPC, buf = 0;
+    info_load<D>(A, base + g, n, b0, list, info[g], lt, S::G);
+    __syncthreads();
+    for (; base < n; base += stride) {
+        const BoxInfo &I = info[buf * S::BPC + g];
+        const int b = I.b;
+        const bool special = b >= 0 && (I.flag & BF_SPECIAL);
+        T rv[S::NIT][S::VEC];
         if (b >= 0) {
-            cb = A.coff[b];
-            special = A.bflag[b] & BF_SPECIAL;
-            const int q0 = special ? 0 : (1 - colour) * Gm::H, q1 = special ? Gm::C : (2 - colour) * Gm::H;
-            load_box<D, M, T>(u, cb, tile, lt, q0, q1);
-            ghosts_phase_a<D, M, T>(A, b, u, tile, lt, Gm::G, colour, hom);
-        }
-        __syncthreads();
-        if (b >= 0 && special) ghosts_phase_b<D, M, T>(A, b, tile, lt, Gm::G, colour);
-        __syncthreads();
-        if (b >= 0) {
-            for (int q = colour * Gm::H + lt; q < (colour + 1) * Gm::H; q += Gm::G) {
-                int i, j, k;
-                rb_cell<D, M>(q, i, j, k);
-                const T s = nb_sum<D, M, T>(tile, i, j, k);
-                u[cb + q] = (s - h2 * rho[cb + q]) * inv;
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, colour, special, hom);
+#pragma unroll
+            for (int it = 0; it < S::NIT; ++it) {
+                const int v = lt + it * S::G;
+                if (v < S::NV) ldv<T, S::VEC>(rho + I.coff + colour * S::H + v * S::VEC, rv[it]);
             }
         }
+        info_load<D>(A, base + stride + g, n, b0, list, info[(buf ^ 1) * S::BPC + g], lt, S::G);
+        __syncthreads();
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, colour);
+        __syncthreads();
+        if (b >= 0) {
+#pragma unroll
+            for (int it = 0; it < S::NIT; ++it) {
+                const int v = lt + it * S::G;
+                if (v < S::NV) {
+                    T out[S::VEC];
+#pragma unroll
+                    for (int x = 0; x < S::VEC; ++x) {
+                        int i, j, k;
+                        rb_cell<D, M>(colour * S::H + v * S::VEC + x, i, j, k);
+                        out[x] = (nb_sum<D, M, T>(tile, i, j, k) - h2 * rv[it][x]) * inv;
+                    }
+                    stv<T, S::VEC>(u + I.coff + colour * S::H + v * S::VEC, out);
+                }
+            }
+        }
+        buf ^= 1;
         __syncthreads();
     }
 }
@@ -270,30 +405,35 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
 template <int D, int M, int MP, typename T>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, int n, T *u, T *rho, T *vold,
                                                              T ih2, int hom) {
+    using S = FullCfg<D, M, T>;
     using Gm = Geo<D, M>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw) + (threadIdx.x / Gm::G) * Gm::PC;
-    const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * (Gm::PC + Gm::C);
+    T *R = tile + Gm::PC;
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (Gm::PC + Gm::C) * S::BPC);
     constexpr int MH = M / 2;
     constexpr int NCO = D == 2 ? MH * MH : MH * MH * MH;
-    for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
-        const int b = resolve_box<D, M>(A, base + g, n, b0, nullptr);
-        bool special = false;
+    const int stride = gridDim.x * S::BPC;
+    int base = blockIdx.x * S::BPC, buf = 0;
+    info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G);
+    __syncthreads();
+    for (; base < n; base += stride) {
+        const BoxInfo &I = info[buf * S::BPC + g];
+        const int b = I.b;
+        const bool special = b >= 0 && (I.flag & BF_SPECIAL);
         if (b >= 0) {
-            special = A.bflag[b] & BF_SPECIAL;
-            load_box<D, M, T>(u, A.coff[b], tile, lt, 0, Gm::C);
-            ghosts_phase_a<D, M, T>(A, b, u, tile, lt, Gm::G, -1, hom);
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom);
+            stage_flat<D, M, T, S::G>(rho + I.coff, R, lt);
         }
+        info_load<D>(A, base + stride + g, n, b0, nullptr, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
-        if (b >= 0 && special) ghosts_phase_b<D, M, T>(A, b, tile, lt, Gm::G, -1);
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
         __syncthreads();
         if (b >= 0) {
-            const long long cb = A.coff[b];
-            const int p = A.parent[b];
-            const long long cp = A.coff[p];
-            const int po = A.poff[b];
-            for (int c = lt; c < NCO; c += Gm::G) {
-                const int I = c % MH, J = (c / MH) % MH, K = D == 3 ? c / (MH * MH) : 0;
+            const long long cp = A.coff[I.parent];
+            for (int c = lt; c < NCO; c += S::G) {
+                const int X = c % MH, Y = (c / MH) % MH, Z = D == 3 ? c / (MH * MH) : 0;
                 T su = T(0), sr = T(0);
 #pragma unroll
                 for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
@@ -301,14 +441,15 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
                     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
                         for (int dx = 0; dx < 2; ++dx) {
-                            const int i = 2 * I + dx, j = 2 * J + dy, k = D == 3 ? 2 * K + dz : 0;
+                            const int i = 2 * X + dx, j = 2 * Y + dy, k = D == 3 ? 2 * Z + dz : 0;
                             const T uc = tile[ti<D, M>(i, j, k)];
                             const T lap = (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
                             su += uc;
-                            sr += rho[cb + rbi<D, M>(i, j, k)] - lap;
+                            sr += R[rbi<D, M>(i, j, k)] - lap;
                         }
                 const T w = T(1) / T(1 << D);
-                const int pi = unpack_off(po, 0) + I, pj = unpack_off(po, 1) + J, pk = D == 3 ? unpack_off(po, 2) + K : 0;
+                const int pi = unpack_off(I.poff, 0) + X, pj = unpack_off(I.poff, 1) + Y;
+                const int pk = D == 3 ? unpack_off(I.poff, 2) + Z : 0;
                 const long long q = cp + rbi<D, MP>(pi, pj, pk);
                 const T mu = su * w;
                 u[q] = mu;
@@ -316,6 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
                 rho[q] = sr * w;
             }
         }
+        buf ^= 1;
         __syncthreads();
     }
 }
@@ -328,36 +470,52 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
 template <int D, int M, typename T>
 __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, const T *u, T *rho, T *vold, T ih2,
                                                   int hom) {
+    using S = FullCfg<D, M, T>;
     using Gm = Geo<D, M>;
+    constexpr int VEC = vec_of<T, Gm::H>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw) + (threadIdx.x / Gm::G) * Gm::PC;
-    const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
-    for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
-        const int b = resolve_box<D, M>(A, base + g, n, b0, nullptr);
-        bool refined = false, special = false;
-        if (b >= 0) {
-            refined = A.bflag[b] & BF_REFINED;
-            special = A.bflag[b] & BF_SPECIAL;
-            const long long cb = A.coff[b];
-            if (refined) {
-                load_box<D, M, T>(u, cb, tile, lt, 0, Gm::C);
-                ghosts_phase_a<D, M, T>(A, b, u, tile, lt, Gm::G, -1, hom);
-            } else {
-                for (int q = lt; q < Gm::C; q += Gm::G) vold[cb + q] = u[cb + q];
+    const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * (Gm::PC + Gm::C);
+    T *R = tile + Gm::PC;
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (Gm::PC + Gm::C) * S::BPC);
+    const int stride = gridDim.x * S::BPC;
+    int base = blockIdx.x * S::BPC, buf = 0;
+    info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G);
+    __syncthreads();
+    for (; base < n; base += stride) {
+        const BoxInfo &I = info[buf * S::BPC + g];
+        const int b = I.b;
+        const bool refined = b >= 0 && (I.flag & BF_REFINED);
+        const bool special = refined && (I.flag & BF_SPECIAL);
+        if (refined) {
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom);
+            stage_flat<D, M, T, S::G>(rho + I.coff, R, lt);
+        } else if (b >= 0) {
+            for (int v = lt; v < Gm::C / VEC; v += S::G) {
+                T e[VEC];
+                ldv<T, VEC>(u + I.coff + (long long)v * VEC, e);
+                stv<T, VEC>(vold + I.coff + (long long)v * VEC, e);
             }
         }
+        info_load<D>(A, base + stride + g, n, b0, nullptr, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
-        if (b >= 0 && refined && special) ghosts_phase_b<D, M, T>(A, b, tile, lt, Gm::G, -1);
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
         __syncthreads();
-        if (b >= 0 && refined) {
-            const long long cb = A.coff[b];
-            for (int q = lt; q < Gm::C; q += Gm::G) {
-                int i, j, k;
-                rb_cell<D, M>(q, i, j, k);
-                const T uc = tile[ti<D, M>(i, j, k)];
-                rho[cb + q] += (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
+        if (refined) {
+            for (int v = lt; v < Gm::C / VEC; v += S::G) {
+                T out[VEC];
+#pragma unroll
+                for (int x = 0; x < VEC; ++x) {
+                    const int q = v * VEC + x;
+                    int i, j, k;
+                    rb_cell<D, M>(q, i, j, k);
+                    const T uc = tile[ti<D, M>(i, j, k)];
+                    out[x] = R[q] + (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
+                }
+                stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
             }
         }
+        buf ^= 1;
         __syncthreads();
     }
 }
@@ -458,20 +616,40 @@ __global__ void __launch_bounds__(kThreads) k_restrict_u(BoxMeta A, int b0, int 
     }
 }
 
-// max of a non-negative double through its bit pattern (monotone for x >= 0)
-__device__ __forceinline__ void atomic_max_pos(unsigned long long *p, double v) {
-    atomicMax(p, static_cast<unsigned long long>(__double_as_longlong(v)));
-}
-
-__device__ __forceinline__ double warp_max(double v) {
+// Block-wide max of per-thread values for the tree `tr` (uniform in the
+// block), then one atomic per block.  Non-negative doubles compare like their
+// bit patterns, so the maxima run on the integer pipe.
+__device__ __forceinline__ void flush_max(unsigned long long rm, unsigned long long pm, int tr, bool valid,
+                                          unsigned long long *rmax, unsigned long long *pmax,
+                                          unsigned long long *red) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    for (int o = 16; o > 0; o >>= 1) {
+        rm = max(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        pm = max(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[w] = rm;
+        red[32 + w] = pm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && valid) {
+        unsigned long long a = 0, c = 0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            a = max(a, red[i]);
+            c = max(c, red[32 + i]);
+        }
+        atomicMax(rmax + tr, a);
+        if (pmax) atomicMax(pmax + tr, c);
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// Residual norm on leaf boxes (list): max |rho - A u| and max |rho| per tree,
-// warp-shuffle reductions + one atomic per warp.  Optionally stores the
+// Residual norm on leaf boxes (list): max |rho - A u| and max |rho| per tree.
+// Each thread keeps running maxima over the boxes it visits; they are
+// reduced over the block and committed with one atomic per block whenever
+// the block moves to another tree, and at the end.  Optionally stores the
 // residual, cast to R, into rout (the mixed-precision defect correction).
 // ---------------------------------------------------------------------------
 template <int D, int M, typename T, typename R>
@@ -479,52 +657,85 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
                                                             const T *__restrict__ rho, int hom,
                                                             unsigned long long *rmax, unsigned long long *pmax,
                                                             R *rout) {
+    using S = FullCfg<D, M, T>;
     using Gm = Geo<D, M>;
+    constexpr int VEC = vec_of<T, Gm::H>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw) + (threadIdx.x / Gm::G) * Gm::PC;
-    const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
-    for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
-        const int b = resolve_box<D, M>(A, base + g, n, 0, list);
-        bool special = false;
+    __shared__ unsigned long long red[64];
+    __shared__ int blk_tree[Geo<D, M>::BPC];
+    const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * (Gm::PC + Gm::C);
+    T *RH = tile + Gm::PC;
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (Gm::PC + Gm::C) * S::BPC);
+    const int stride = gridDim.x * S::BPC;
+    int base = blockIdx.x * S::BPC, buf = 0;
+    info_load<D>(A, base + g, n, 0, list, info[g], lt, S::G);
+    __syncthreads();
+    unsigned long long rm = 0, pm = 0;
+    int cur = -1;  // tree of the running maxima (uniform in the block)
+    for (; base < n; base += stride) {
+        const BoxInfo &I = info[buf * S::BPC + g];
+        const int b = I.b;
+        const bool special = b >= 0 && (I.flag & BF_SPECIAL);
+        double h = 1.0;
         if (b >= 0) {
-            special = A.bflag[b] & BF_SPECIAL;
-            load_box<D, M, T>(u, A.coff[b], tile, lt, 0, Gm::C);
-            ghosts_phase_a<D, M, T>(A, b, u, tile, lt, Gm::G, -1, hom);
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom);
+            stage_flat<D, M, T, S::G>(rho + I.coff, RH, lt);
+            h = A.hb[b];
         }
+        if (lt == 0) blk_tree[g] = b >= 0 ? A.tree[b] : -1;
+        info_load<D>(A, base + stride + g, n, 0, list, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
-        if (b >= 0 && special) ghosts_phase_b<D, M, T>(A, b, tile, lt, Gm::G, -1);
+        // the block's boxes all belong to one tree unless the tree changes here
+        int tr = -1;
+        bool mixed = false;
+        for (int x = 0; x < S::BPC; ++x) {
+            const int t = blk_tree[x];
+            if (t < 0) continue;
+            if (tr < 0) tr = t;
+            else if (t != tr) mixed = true;
+        }
+        if (mixed || (tr >= 0 && cur >= 0 && tr != cur)) {
+            flush_max(rm, pm, cur, cur >= 0, rmax, pmax, red);
+            rm = pm = 0;
+            cur = -1;
+        }
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
         __syncthreads();
-        double rm = 0.0, pm = 0.0;
-        int tr = 0;
         if (b >= 0) {
-            const long long cb = A.coff[b];
-            tr = A.tree[b];
-            const T ih2 = T(1.0 / (A.hb[b] * A.hb[b]));
-            for (int q = lt; q < Gm::C; q += Gm::G) {
-                int i, j, k;
-                rb_cell<D, M>(q, i, j, k);
-                const T uc = tile[ti<D, M>(i, j, k)];
-                const T rr = rho[cb + q] - (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
-                if (rout) rout[cb + q] = R(rr);
-                rm = fmax(rm, fabs(double(rr)));
-                pm = fmax(pm, fabs(double(rho[cb + q])));
+            const T ih2 = T(1.0 / (h * h));
+            for (int v = lt; v < Gm::C / VEC; v += S::G) {
+                R out[VEC];
+#pragma unroll
+                for (int x = 0; x < VEC; ++x) {
+                    const int q = v * VEC + x;
+                    int i, j, k;
+                    rb_cell<D, M>(q, i, j, k);
+                    const T uc = tile[ti<D, M>(i, j, k)];
+                    const T rr = RH[q] - (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
+                    out[x] = R(rr);
+                    rm = max(rm, (unsigned long long)__double_as_longlong(fabs(double(rr))));
+                    pm = max(pm, (unsigned long long)__double_as_longlong(fabs(double(RH[q]))));
+                }
+                if (rout) {
+#pragma unroll
+                    for (int x = 0; x < VEC; ++x) rout[I.coff + (long long)v * VEC + x] = out[x];
+                }
             }
         }
-        // groups never straddle a warp boundary unless G >= 32, so a warp holds one tree
-        // when G >= 32; for smaller groups reduce per thread
-        if (Gm::G >= 32) {
-            rm = warp_max(rm);
-            pm = warp_max(pm);
-            if ((threadIdx.x & 31) == 0 && b >= 0) {
-                atomic_max_pos(rmax + tr, rm);
-                if (pmax) atomic_max_pos(pmax + tr, pm);
+        if (mixed) {  // boxes of several trees in this block: commit each box's maxima now
+            for (int x = 0; x < S::BPC; ++x) {
+                const int t = blk_tree[x];
+                flush_max(g == x ? rm : 0ull, g == x ? pm : 0ull, t, t >= 0, rmax, pmax, red);
             }
-        } else if (b >= 0) {
-            atomic_max_pos(rmax + tr, rm);
-            if (pmax) atomic_max_pos(pmax + tr, pm);
+            rm = pm = 0;
+        } else if (tr >= 0) {
+            cur = tr;
         }
+        buf ^= 1;
         __syncthreads();
     }
+    flush_max(rm, pm, cur, cur >= 0, rmax, pmax, red);
 }
 
 }  // namespace afg

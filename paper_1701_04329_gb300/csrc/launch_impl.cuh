@@ -28,10 +28,11 @@ template <int D, int M, typename T>
 void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
                double h2, int colour, int hom) {
     if (n <= 0) return;
-    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    using S = SmCfg<D, M, T>;
+    const size_t smem = S::smem();
     auto k = k_smooth<D, M, T>;
-    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, list, (T *)u, (const T *)rho,
-                                                                          T(h2), colour, hom);
+    k<<<grid_for(k, smem, (n + S::BPC - 1) / S::BPC), kThreads, smem, c.stream>>>(A, b0, n, list, (T *)u,
+                                                                                (const T *)rho, T(h2), colour, hom);
     ++g_launches;
 }
 
@@ -39,7 +40,7 @@ template <int D, int M, int MP, typename T>
 void do_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
                        double ih2, int hom) {
     if (n <= 0) return;
-    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    const size_t smem = FullCfg<D, M, T>::smem();
     auto k = k_resid_restrict<D, M, MP, T>;
     k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (T *)u, (T *)rho, (T *)vold,
                                                                           T(ih2), hom);
@@ -50,7 +51,7 @@ template <int D, int M, typename T>
 void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold, double ih2,
             int hom) {
     if (n <= 0) return;
-    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    const size_t smem = FullCfg<D, M, T>::smem();
     auto k = k_fas<D, M, T>;
     k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (const T *)u, (T *)rho,
                                                                           (T *)vold, T(ih2), hom);
@@ -80,7 +81,7 @@ void do_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int
                       int hom, unsigned long long *rmax, unsigned long long *pmax, void *rout,
                       bool rout_f32) {
     if (n <= 0) return;
-    const size_t smem = sizeof(T) * Geo<D, M>::PC * Geo<D, M>::BPC;
+    const size_t smem = FullCfg<D, M, T>::smem();
     if (rout_f32) {
         auto k = k_leaf_residual<D, M, T, float>;
         k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(
