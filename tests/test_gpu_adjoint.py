@@ -71,7 +71,7 @@ def test_autograd_gradient_vs_central_differences():
     L.backward()
     gr, gb = rho.grad.clone(), b.grad.clone()
     for i in rng.choice(t.n_leaf_cells, 20, replace=False):
-        h = 1e-6 * max(1.0, abs(float(rho[i])))
+        h = 1e-6 * max(1.0, abs(float(rho.detach()[i])))
         with torch.no_grad():
             rp = rho.detach().clone(); rp[i] += h
             rm = rho.detach().clone(); rm[i] -= h
