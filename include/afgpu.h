@@ -182,6 +182,27 @@ int afg_forest_get_solution(const afg_forest *f, double *u_dev);
  * later cycles.  per_tree (may be NULL) receives n stats records. */
 int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree);
 
+/* Allocation-free residual norms of a forest.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * where they check convergence -- e.g. a host framework that has handed the
+ * whole device memory pool to its own caching allocator, or a latency-bound
+ * loop in which the implicit device synchronisation of cudaMalloc/cudaFree is
+ * not acceptable.  It computes the same per-tree values as the norms that
+ * afg_forest_solve reports (max over leaf cells of |rho - A u| and of |rho|,
+ * composite operator, for the forest's current solution) and writes them to
+ * the host arrays max_abs_r[n] and max_abs_rho[n] (n = trees).  It calls no
+ * cudaMalloc/cudaFree: besides the forest's own data it uses one file-scope
+ * device array of 2 x 1024 eight-byte slots (16 KB held by every GPU that
+ * loads the library until the process exits); forests of more than 1024
+ * trees are rejected with AFG_ERR_ARG.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) and must come before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents (the slots are cleared at the start of every call), so
+ * calls whose GPU work overlaps race with each other.  The forest must have
+ * been created (its device data exists); the call synchronises the forest's
+ * stream. */
+int afg_forest_residual_norms_noalloc(afg_forest *f, double *max_abs_r, double *max_abs_rho);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 
 /* Total number of this library's kernels launched so far in this process,

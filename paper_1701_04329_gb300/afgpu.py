@@ -63,6 +63,7 @@ _SIGS = {
     "afg_forest_set_dirichlet": (I, [P, P]), "afg_forest_get_solution": (I, [P, P]),
     "afg_forest_solve": (I, [P, P, P]), "afg_kernel_launches": (I, [P]),
     "afg_time_kernel": (I, [P, I, I, I, I, P, P, P, P]),
+    "afg_forest_residual_norms_noalloc": (I, [P, P, P]),
 }
 
 
@@ -311,6 +312,14 @@ class Forest:
             out = torch.empty(int(self.cells.sum()), dtype=torch.float64, device="cuda")
         _check(lib().afg_forest_get_solution(self._h, _dev(out, int(self.cells.sum()))))
         return out
+
+    def residual_norms_noalloc(self):
+        """Per-tree (max|r|, max|rho|) through the allocation-free entry point."""
+        self._sync_stream()
+        r = np.zeros(self.T)
+        p = np.zeros(self.T)
+        _check(lib().afg_forest_residual_norms_noalloc(self._h, r.ctypes.data_as(P), p.ctypes.data_as(P)))
+        return r, p
 
     def solve(self, opts=None, allow_not_converged=False):
         self._sync_stream()

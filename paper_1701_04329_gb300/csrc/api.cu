@@ -11,25 +11,11 @@
 #include <vector>
 
 #include "../../include/afgpu.h"
-#include "grid.h"
+#include "handles.h"
 
 using afg::Grid;
 using afg::HostTree;
 using afg::HBox;
-
-struct afg_tree {
-    HostTree ht;
-    std::unique_ptr<Grid> grid;
-    int grid_version = -1;
-    cudaStream_t stream = nullptr;
-    afg_tree(int d, int n, int m) : ht(d, n, m) {}
-};
-
-struct afg_forest {
-    std::vector<std::unique_ptr<HostTree>> trees;
-    std::unique_ptr<Grid> grid;
-    cudaStream_t stream = nullptr;
-};
 
 namespace {
 thread_local std::string g_err;
@@ -147,6 +133,12 @@ void fill_stats(afg_stats *st, const Grid &g, int t, int cycles, double secs) {
 }
 
 using clk = std::chrono::steady_clock;
+
+}  // namespace
+
+int afg::api_fail(int code, const std::string &msg) { return fail(code, msg); }
+
+namespace {
 
 // FMG then V-cycles (plain FP64), all trees of the grid together; a tree that
 // reached rel_tol is masked out of later cycles.  Returns cycles done.
