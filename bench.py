@@ -45,9 +45,38 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", choices=["smooth", "resid", "correct", "leafres"],
                     help="time one kernel on a uniform tree of --uniform-level (profiling case)")
+    ap.add_argument("--solve-only", choices=["fp64", "mixed"],
+                    help="only --steps solves of the benchmark workload (profiling case)")
     ap.add_argument("--fp32", action="store_true")
     ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
+
+
+def solve_only(args):
+    """--warmup + --steps solves of the benchmark workload, nothing else."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    from paper_1701_04329_gb300 import workloads as W
+    p = W.twosrc3d(uniform_level=args.uniform_level)
+    t = afgpu.Tree(p.dim, p.box_n, p.max_level)
+    p.build(t)
+    rho_h, b_h = p.data(t)
+    rho, bv = torch.tensor(rho_h, device="cuda"), torch.tensor(b_h, device="cuda")
+    zero = torch.zeros_like(rho)
+    prec = afgpu.AFG_MIXED if args.solve_only == "mixed" else afgpu.AFG_FP64
+    opts = afgpu.default_opts(rel_tol=args.tol, precision=prec)
+    t.set_rhs(rho)
+    t.set_dirichlet(bv)
+    ms = []
+    for i in range(args.warmup + args.steps):
+        t.set_solution(zero)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = t.solve(opts)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms.append((time.perf_counter() - t0) * 1e3)
+    print(json.dumps({"solve": args.solve_only, "ms": ms, "cycles": st["cycles"], "rel": st["rel_residual"]}))
 
 
 def kernel_only(args):
@@ -201,6 +230,9 @@ def main():
     args = parse()
     if args.kernel_only:
         kernel_only(args)
+        return
+    if args.solve_only:
+        solve_only(args)
         return
     if args.impl == "reference":
         run_reference(args)

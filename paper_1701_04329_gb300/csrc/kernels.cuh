@@ -191,9 +191,55 @@ __device__ __forceinline__ void face_cell(int f, int only, int pin, int &t1, int
 // `only` < 0: all side ghosts; otherwise only the ghosts next to interior
 // cells of colour `only` (all a half-sweep of that colour reads).
 // ---------------------------------------------------------------------------
+// Index tables of a CTA (built once per launch in shared memory):
+//   tix[q]      tile index of storage position q (both colours)
+//   gt[item]    tile slot of ghost item (side s, face cell f) for the launch's `only`
+//   gs[item]    storage index, in the same-level neighbour, of that ghost's source cell
+template <int D, int M>
+struct Tables {
+    static constexpr int C = Geo<D, M>::C, F = Geo<D, M>::F;
+    static constexpr size_t bytes() { return sizeof(short) * (C + 2 * 2 * D * F); }
+};
+
+template <int D, int M>
+__device__ __forceinline__ void build_tables(short *tix, short *gt, short *gs, int only) {
+    constexpr int C = Geo<D, M>::C, F = Geo<D, M>::F;
+    for (int q = threadIdx.x; q < C; q += blockDim.x) {
+        int i, j, k;
+        rb_cell<D, M>(q, i, j, k);
+        tix[q] = (short)ti<D, M>(i, j, k);
+    }
+    const int nf = only < 0 ? F : F / 2;
+    for (int item = threadIdx.x; item < 2 * D * nf; item += blockDim.x) {
+        const int s = item / nf, f = item - s * nf;
+        const int hi = s & 1;
+        int t1, t2;
+        face_cell<D, M>(f, only, hi ? M - 1 : 0, t1, t2);
+        int i, j, k;
+        face_pos(D, s, hi ? M : -1, t1, t2, i, j, k);
+        gt[item] = (short)ti<D, M>(i, j, k);
+        face_pos(D, s, hi ? 0 : M - 1, t1, t2, i, j, k);
+        gs[item] = (short)rbi<D, M>(i, j, k);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Box staging.  gather() issues every global load of a box at once: the
+// interior colour halves as 16-byte vectors, and the side ghosts of all
+// sides together -- the neighbour's face cell (same level), the Dirichlet
+// value b (domain boundary) or the coarse value u_H (refinement boundary).
+// finalize(), after a barrier, turns the last two into ghost values with
+// the box's own cells (Sec. 2.4 and the default scheme of Sec. 3.3):
+//   Dirichlet:           g = 2 b - u_1
+//   refinement boundary: 2D g = u_H/2 + u_1 - (u_t + u_2)/4
+//                        3D g = u_H/2 + 5/4 u_1 - (u_2 + u_t1 + u_t2)/4
+// `only` < 0: all side ghosts; otherwise only the ghosts next to interior
+// cells of colour `only` (all a half-sweep of that colour reads).
+// ---------------------------------------------------------------------------
 template <int D, int M, typename T, int G>
 __device__ __forceinline__ void gather(const BoxInfo &I, const T *__restrict__ u, const double *__restrict__ bc,
-                                       T *tile, int lt, int only, bool own, int hom) {
+                                       T *tile, int lt, int only, bool own, int hom, const short *tix,
+                                       const short *gt, const short *gs) {
     constexpr int C = Geo<D, M>::C, H = Geo<D, M>::H, F = Geo<D, M>::F;
     constexpr int VEC = vec_of<T, H>();
     const int q0 = (only < 0 || own) ? 0 : (1 - only) * H;
@@ -202,38 +248,33 @@ __device__ __forceinline__ void gather(const BoxInfo &I, const T *__restrict__ u
         T e[VEC];
         ldv<T, VEC>(u + I.coff + (long long)v * VEC, e);
 #pragma unroll
-        for (int x = 0; x < VEC; ++x) {
-            int i, j, k;
-            rb_cell<D, M>(v * VEC + x, i, j, k);
-            tile[ti<D, M>(i, j, k)] = e[x];
-        }
+        for (int x = 0; x < VEC; ++x) tile[tix[v * VEC + x]] = e[x];
     }
     const int nf = only < 0 ? F : F / 2;
     for (int item = lt; item < 2 * D * nf; item += G) {
-        const int s = item / nf, f = item - s * nf;
+        const int s = item / nf;
         const int code = I.code[s];
         const long long base = I.base[s];
-        const int hi = s & 1, a = s >> 1;
-        int t1, t2;
-        face_cell<D, M>(f, only, hi ? M - 1 : 0, t1, t2);
-        int i, j, k;
-        face_pos(D, s, hi ? M : -1, t1, t2, i, j, k);
         T v;
         if (code >= 0) {
-            int mi, mj, mk;
-            face_pos(D, s, hi ? 0 : M - 1, t1, t2, mi, mj, mk);
-            v = u[base + rbi<D, M>(mi, mj, mk)];
-        } else if (code == -1) {
-            v = hom ? T(0) : T(bc[base + t2 * M + t1]);
+            v = u[base + gs[item]];
         } else {
-            const int ta1 = a == 0 ? 1 : 0, ta2 = a == 2 ? 1 : 2;
-            const int c1 = unpack_off(I.poff, ta1) + (t1 >> 1);
-            const int c2 = D == 3 ? unpack_off(I.poff, ta2) + (t2 >> 1) : 0;
-            int ci, cj, ck;
-            face_pos(D, s, hi ? 0 : M - 1, c1, c2, ci, cj, ck);
-            v = u[base + rbi<D, M>(ci, cj, ck)];
+            const int f = item - s * nf;
+            const int hi = s & 1, a = s >> 1;
+            int t1, t2;
+            face_cell<D, M>(f, only, hi ? M - 1 : 0, t1, t2);
+            if (code == -1) {
+                v = hom ? T(0) : T(bc[base + t2 * M + t1]);
+            } else {
+                const int ta1 = a == 0 ? 1 : 0, ta2 = a == 2 ? 1 : 2;
+                const int c1 = unpack_off(I.poff, ta1) + (t1 >> 1);
+                const int c2 = D == 3 ? unpack_off(I.poff, ta2) + (t2 >> 1) : 0;
+                int ci, cj, ck;
+                face_pos(D, s, hi ? 0 : M - 1, c1, c2, ci, cj, ck);
+                v = u[base + rbi<D, M>(ci, cj, ck)];
+            }
         }
-        tile[ti<D, M>(i, j, k)] = v;
+        tile[gt[item]] = v;
     }
 }
 
@@ -313,6 +354,19 @@ __device__ __forceinline__ void stage_flat(const T *__restrict__ src, T *dst, in
     }
 }
 
+// vector copy of a box's C values into a padded tile through tix
+template <int D, int M, typename T, int G>
+__device__ __forceinline__ void stage_tile(const T *__restrict__ src, T *dst, int lt, const short *tix) {
+    constexpr int C = Geo<D, M>::C;
+    constexpr int VEC = vec_of<T, Geo<D, M>::H>();
+    for (int v = lt; v < C / VEC; v += G) {
+        T e[VEC];
+        ldv<T, VEC>(src + (long long)v * VEC, e);
+#pragma unroll
+        for (int x = 0; x < VEC; ++x) dst[tix[v * VEC + x]] = e[x];
+    }
+}
+
 // Launch geometry of the half-sweep: one thread per 16-byte vector of a
 // colour half (capped at the CTA size).
 template <int D, int M, typename T>
@@ -323,7 +377,9 @@ struct SmCfg {
     static constexpr int G = NV < kThreads ? NV : kThreads;
     static constexpr int BPC = kThreads / G;
     static constexpr int NIT = (NV + G - 1) / G;
-    static constexpr size_t smem() { return sizeof(T) * Geo<D, M>::PC * BPC + 2 * sizeof(BoxInfo) * BPC; }
+    static constexpr size_t smem() {
+        return sizeof(T) * Geo<D, M>::PC * BPC + 2 * sizeof(BoxInfo) * BPC + Tables<D, M>::bytes();
+    }
 };
 
 // Launch geometry of the full-box kernels (residual, FAS): a tile plus the
@@ -333,9 +389,28 @@ struct FullCfg {
     static constexpr int G = Geo<D, M>::G;
     static constexpr int BPC = Geo<D, M>::BPC;
     static constexpr size_t smem() {
-        return sizeof(T) * (Geo<D, M>::PC + Geo<D, M>::C) * BPC + 2 * sizeof(BoxInfo) * BPC;
+        return sizeof(T) * 2 * Geo<D, M>::PC * BPC + 2 * sizeof(BoxInfo) * BPC + Tables<D, M>::bytes();
     }
 };
+
+// sum of the 2D face neighbours of tile slot t, ((x-+x+)+(y-+y+))+(z-+z+)
+template <int D, int M, typename T>
+__device__ __forceinline__ T nb_sum_t(const T *tile, int t) {
+    constexpr int P = M + 2;
+    T s = (tile[t - 1] + tile[t + 1]) + (tile[t - P] + tile[t + P]);
+    if (D == 3) s += tile[t - P * P] + tile[t + P * P];
+    return s;
+}
+
+// shared-memory carve-up: tiles, then the double-buffered BoxInfo, then tables
+template <int D, int M>
+__device__ __forceinline__ void carve(unsigned char *raw, size_t tiles_bytes, int bpc, BoxInfo *&info, short *&tix,
+                                      short *&gt, short *&gs) {
+    info = reinterpret_cast<BoxInfo *>(raw + tiles_bytes);
+    tix = reinterpret_cast<short *>(raw + tiles_bytes + 2 * sizeof(BoxInfo) * bpc);
+    gt = tix + Geo<D, M>::C;
+    gs = gt + 2 * D * Geo<D, M>::F;
+}
 
 // ---------------------------------------------------------------------------
 // Red-black Gauss-Seidel half-sweep on every box of a level (Sec. 3.1):
@@ -352,7 +427,10 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
     T *tile = reinterpret_cast<T *>(smem_raw) + g * Gm::PC;
-    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * Gm::PC * S::BPC);
+    BoxInfo *info;
+    short *tix, *gt, *gs;
+    carve<D, M>(smem_raw, sizeof(T) * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    build_tables<D, M>(tix, gt, gs, colour);
     const T inv = T(1) / T(2 * D);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
@@ -364,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
         const bool special = b >= 0 && (I.flag & BF_SPECIAL);
         T rv[S::NIT][S::VEC];
         if (b >= 0) {
-            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, colour, special, hom);
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, colour, special, hom, tix, gt, gs);
 #pragma unroll
             for (int it = 0; it < S::NIT; ++it) {
                 const int v = lt + it * S::G;
@@ -383,9 +461,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
                     T out[S::VEC];
 #pragma unroll
                     for (int x = 0; x < S::VEC; ++x) {
-                        int i, j, k;
-                        rb_cell<D, M>(colour * S::H + v * S::VEC + x, i, j, k);
-                        out[x] = (nb_sum<D, M, T>(tile, i, j, k) - h2 * rv[it][x]) * inv;
+                        const int t = tix[colour * S::H + v * S::VEC + x];
+                        out[x] = (nb_sum_t<D, M, T>(tile, t) - h2 * rv[it][x]) * inv;
                     }
                     stv<T, S::VEC>(u + I.coff + colour * S::H + v * S::VEC, out);
                 }
@@ -407,11 +484,15 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
                                                              T ih2, int hom) {
     using S = FullCfg<D, M, T>;
     using Gm = Geo<D, M>;
+    constexpr int P = M + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
-    T *tile = reinterpret_cast<T *>(smem_raw) + g * (Gm::PC + Gm::C);
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * 2 * Gm::PC;
     T *R = tile + Gm::PC;
-    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (Gm::PC + Gm::C) * S::BPC);
+    BoxInfo *info;
+    short *tix, *gt, *gs;
+    carve<D, M>(smem_raw, sizeof(T) * 2 * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    build_tables<D, M>(tix, gt, gs, -1);
     constexpr int MH = M / 2;
     constexpr int NCO = D == 2 ? MH * MH : MH * MH * MH;
     const int stride = gridDim.x * S::BPC;
@@ -423,8 +504,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
         const int b = I.b;
         const bool special = b >= 0 && (I.flag & BF_SPECIAL);
         if (b >= 0) {
-            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom);
-            stage_flat<D, M, T, S::G>(rho + I.coff, R, lt);
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom, tix, gt, gs);
+            stage_tile<D, M, T, S::G>(rho + I.coff, R, lt, tix);
         }
         info_load<D>(A, base + stride + g, n, b0, nullptr, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
@@ -434,6 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
             const long long cp = A.coff[I.parent];
             for (int c = lt; c < NCO; c += S::G) {
                 const int X = c % MH, Y = (c / MH) % MH, Z = D == 3 ? c / (MH * MH) : 0;
+                const int t0 = ti<D, M>(2 * X, 2 * Y, D == 3 ? 2 * Z : 0);
                 T su = T(0), sr = T(0);
 #pragma unroll
                 for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
@@ -441,11 +523,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
                     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
                         for (int dx = 0; dx < 2; ++dx) {
-                            const int i = 2 * X + dx, j = 2 * Y + dy, k = D == 3 ? 2 * Z + dz : 0;
-                            const T uc = tile[ti<D, M>(i, j, k)];
-                            const T lap = (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
+                            const int t = t0 + dx + dy * P + dz * P * P;
+                            const T uc = tile[t];
+                            const T lap = (nb_sum_t<D, M, T>(tile, t) - T(2 * D) * uc) * ih2;
                             su += uc;
-                            sr += R[rbi<D, M>(i, j, k)] - lap;
+                            sr += R[t] - lap;
                         }
                 const T w = T(1) / T(1 << D);
                 const int pi = unpack_off(I.poff, 0) + X, pj = unpack_off(I.poff, 1) + Y;
@@ -475,9 +557,12 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
     constexpr int VEC = vec_of<T, Gm::H>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
-    T *tile = reinterpret_cast<T *>(smem_raw) + g * (Gm::PC + Gm::C);
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * 2 * Gm::PC;
     T *R = tile + Gm::PC;
-    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (Gm::PC + Gm::C) * S::BPC);
+    BoxInfo *info;
+    short *tix, *gt, *gs;
+    carve<D, M>(smem_raw, sizeof(T) * 2 * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    build_tables<D, M>(tix, gt, gs, -1);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
     info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G);
@@ -488,7 +573,7 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
         const bool refined = b >= 0 && (I.flag & BF_REFINED);
         const bool special = refined && (I.flag & BF_SPECIAL);
         if (refined) {
-            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom);
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom, tix, gt, gs);
             stage_flat<D, M, T, S::G>(rho + I.coff, R, lt);
         } else if (b >= 0) {
             for (int v = lt; v < Gm::C / VEC; v += S::G) {
@@ -507,10 +592,8 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
 #pragma unroll
                 for (int x = 0; x < VEC; ++x) {
                     const int q = v * VEC + x;
-                    int i, j, k;
-                    rb_cell<D, M>(q, i, j, k);
-                    const T uc = tile[ti<D, M>(i, j, k)];
-                    out[x] = R[q] + (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
+                    const int t = tix[q];
+                    out[x] = R[q] + (nb_sum_t<D, M, T>(tile, t) - T(2 * D) * tile[t]) * ih2;
                 }
                 stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
             }
@@ -664,9 +747,12 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
     __shared__ unsigned long long red[64];
     __shared__ int blk_tree[Geo<D, M>::BPC];
     const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
-    T *tile = reinterpret_cast<T *>(smem_raw) + g * (Gm::PC + Gm::C);
+    T *tile = reinterpret_cast<T *>(smem_raw) + g * 2 * Gm::PC;
     T *RH = tile + Gm::PC;
-    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (Gm::PC + Gm::C) * S::BPC);
+    BoxInfo *info;
+    short *tix, *gt, *gs;
+    carve<D, M>(smem_raw, sizeof(T) * 2 * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    build_tables<D, M>(tix, gt, gs, -1);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
     info_load<D>(A, base + g, n, 0, list, info[g], lt, S::G);
@@ -679,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
         const bool special = b >= 0 && (I.flag & BF_SPECIAL);
         double h = 1.0;
         if (b >= 0) {
-            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom);
+            gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom, tix, gt, gs);
             stage_flat<D, M, T, S::G>(rho + I.coff, RH, lt);
             h = A.hb[b];
         }
@@ -709,10 +795,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
 #pragma unroll
                 for (int x = 0; x < VEC; ++x) {
                     const int q = v * VEC + x;
-                    int i, j, k;
-                    rb_cell<D, M>(q, i, j, k);
-                    const T uc = tile[ti<D, M>(i, j, k)];
-                    const T rr = RH[q] - (nb_sum<D, M, T>(tile, i, j, k) - T(2 * D) * uc) * ih2;
+                    const int t = tix[q];
+                    const T rr = RH[q] - (nb_sum_t<D, M, T>(tile, t) - T(2 * D) * tile[t]) * ih2;
                     out[x] = R(rr);
                     rm = max(rm, (unsigned long long)__double_as_longlong(fabs(double(rr))));
                     pm = max(pm, (unsigned long long)__double_as_longlong(fabs(double(RH[q]))));

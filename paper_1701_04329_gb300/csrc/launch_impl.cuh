@@ -6,6 +6,7 @@
 #include <string>
 
 #include "kernels_leaf.cuh"
+#include "kernels_smooth.cuh"
 #include "launch.h"
 
 namespace afg {
@@ -28,11 +29,19 @@ template <int D, int M, typename T>
 void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
                double h2, int colour, int hom) {
     if (n <= 0) return;
-    using S = SmCfg<D, M, T>;
-    const size_t smem = S::smem();
-    auto k = k_smooth<D, M, T>;
-    k<<<grid_for(k, smem, (n + S::BPC - 1) / S::BPC), kThreads, smem, c.stream>>>(A, b0, n, list, (T *)u,
-                                                                                (const T *)rho, T(h2), colour, hom);
+    if constexpr (SvCfg<D, M, T>::ok && sizeof(T) == 4) {  // FP64 keeps k_smooth: fewer registers, FP64-bound anyway
+        using S = SvCfg<D, M, T>;
+        const size_t smem = S::smem();
+        auto k = k_smooth_v<D, M, T>;
+        k<<<grid_for(k, smem, (n + S::BPC - 1) / S::BPC), kThreads, smem, c.stream>>>(
+            A, b0, n, list, (T *)u, (const T *)rho, T(h2), colour, hom);
+    } else {
+        using S = SmCfg<D, M, T>;
+        const size_t smem = S::smem();
+        auto k = k_smooth<D, M, T>;
+        k<<<grid_for(k, smem, (n + S::BPC - 1) / S::BPC), kThreads, smem, c.stream>>>(
+            A, b0, n, list, (T *)u, (const T *)rho, T(h2), colour, hom);
+    }
     ++g_launches;
 }
 
