@@ -47,9 +47,54 @@ def parse():
                     help="time one kernel on a uniform tree of --uniform-level (profiling case)")
     ap.add_argument("--solve-only", choices=["fp64", "mixed"],
                     help="only --steps solves of the benchmark workload (profiling case)")
+    ap.add_argument("--forest", type=int, default=0,
+                    help="batched 2D workload with this many trees: autotune, then time (not the headline)")
+    ap.add_argument("--paper-cmp", action="store_true",
+                    help="one FMG cycle on the uniform 512^3 problem of the paper's scaling test")
     ap.add_argument("--fp32", action="store_true")
     ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
+
+
+def forest_mode(args):
+    """Batched 2D workload: N independent quadtrees (seeds 1000+t, 1-4 Gaussian
+    sources, max level 4..9), mixed precision, autotuned box size and sweeps."""
+    from paper_1701_04329_gb300 import autotune
+    best, table = autotune.autotune_forest(args.forest, tol=args.tol, reps=args.steps)
+    print(json.dumps({"workload": "batched 2D forest, %d trees" % args.forest, "tol": args.tol,
+                      "best": best, "table": table}), flush=True)
+
+
+def paper_cmp(args):
+    """The paper's Sec. 4.2 problem: Laplacian(phi) = 1, phi = 0 on [0,1]^3,
+    uniform 512^3 (1.34e8 unknowns), boxes 8^3, one FMG cycle with (2,2,4)."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    from paper_1701_04329_gb300 import workloads as W
+    p = W.uniform3d(level=7)
+    t = afgpu.Tree(3, 8, 7)
+    t.refine_uniform(7)
+    n = t.n_leaf_cells
+    t.set_rhs(torch.ones(n, dtype=torch.float64, device="cuda"))
+    zero = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = {"workload": "uniform 512^3, Laplacian(phi)=1, phi=0, 8^3 boxes, one FMG (2,2,4)", "unknowns": n}
+    for name, prec in (("fp64", afgpu.AFG_FP64), ("mixed", afgpu.AFG_MIXED)):
+        opts = afgpu.default_opts(precision=prec, rel_tol=0.0, max_cycles=1)
+        ms = []
+        for i in range(args.warmup + args.steps):
+            t.set_solution(zero)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if prec == afgpu.AFG_FP64:
+                st = t.fmg(opts)
+            else:
+                st = t.solve(opts, allow_not_converged=True)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ms.append((time.perf_counter() - t0) * 1e3)
+        out[name] = {"ms_per_fmg": min(ms), "ns_per_unknown": min(ms) * 1e6 / n, "rel_residual": st["rel_residual"]}
+    out["paper_ns_per_unknown_8cubed_16_cores"] = 22.0
+    print(json.dumps(out), flush=True)
 
 
 def solve_only(args):
@@ -233,6 +278,12 @@ def main():
         return
     if args.solve_only:
         solve_only(args)
+        return
+    if args.forest:
+        forest_mode(args)
+        return
+    if args.paper_cmp:
+        paper_cmp(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -11,21 +11,22 @@ from . import afgpu
 
 
 class PoissonSolve(torch.autograd.Function):
-    """u = PoissonSolve.apply(rho, b, tree, opts): rho on leaf cells, b on leaf
-    boundary faces (canonical orders, float64 CUDA tensors)."""
+    """u = PoissonSolve.apply(rho, b, tree, opts, adj_opts): rho on leaf cells,
+    b on leaf boundary faces (canonical orders, float64 CUDA tensors); opts
+    control the forward solve, adj_opts (default: opts) the adjoint solve."""
 
     @staticmethod
-    def forward(ctx, rho, b, tree, opts=None):
+    def forward(ctx, rho, b, tree, opts=None, adj_opts=None):
         opts = opts or afgpu.default_opts()
         tree.set_rhs(rho.detach().contiguous())
         if b.numel():
             tree.set_dirichlet(b.detach().contiguous())
         tree.set_solution(torch.zeros_like(rho))
         tree.solve(opts)
-        ctx.tree, ctx.opts, ctx.nb = tree, opts, b.numel()
+        ctx.tree, ctx.opts, ctx.nb = tree, adj_opts or opts, b.numel()
         return tree.get_solution()
 
     @staticmethod
     def backward(ctx, gu):
         lam, db, _ = ctx.tree.adjoint(gu.detach().contiguous(), ctx.opts)
-        return lam, db[: ctx.nb], None, None
+        return lam, db[: ctx.nb], None, None, None

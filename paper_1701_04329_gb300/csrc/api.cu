@@ -148,6 +148,7 @@ int solve_fp64(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::v
     const bool forest = g.T > 1;
     std::vector<int> ones(g.T, 1);
     check(cudaMemcpyAsync(g.d_converged_mask(), ones.data(), g.T * sizeof(int), cudaMemcpyHostToDevice, s), "mask");
+    g.set_tol(o.rel_tol, s);
     int cycles = 0;
     hist.assign(g.T, {});
     auto record = [&]() {
@@ -158,12 +159,12 @@ int solve_fp64(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::v
         run(g, {1, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) {
             g.fmg(g.ws64, mo, 0, forest, cs);
             g.norms_async(g.ws64, 0, nullptr, false, cs);
-            g.mask_update_async(o.rel_tol, cs);
+            g.mask_update_async(cs);
         });
     } else {
         run(g, {3, 0, 0, 0, 0}, o.use_graph, s, [&](cudaStream_t cs) {
             g.norms_async(g.ws64, 0, nullptr, false, cs);
-            g.mask_update_async(o.rel_tol, cs);
+            g.mask_update_async(cs);
         });
     }
     check(cudaStreamSynchronize(s), "solve");
@@ -173,7 +174,7 @@ int solve_fp64(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::v
         run(g, {2, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) {
             g.vcycle(g.ws64, g.lmax, mo, 0, forest ? g.d_converged_mask() : nullptr, cs);
             g.norms_async(g.ws64, 0, nullptr, false, cs);
-            g.mask_update_async(o.rel_tol, cs);
+            g.mask_update_async(cs);
         });
         check(cudaStreamSynchronize(s), "solve");
         ++cycles;
@@ -193,6 +194,7 @@ int solve_mixed(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::
     const bool forest = g.T > 1;
     std::vector<int> ones(g.T, 1);
     check(cudaMemcpyAsync(g.d_converged_mask(), ones.data(), g.T * sizeof(int), cudaMemcpyHostToDevice, s), "mask");
+    g.set_tol(o.rel_tol, s);
     hist.assign(g.T, {});
     auto record = [&]() {
         for (int t = 0; t < g.T; ++t)
@@ -201,7 +203,7 @@ int solve_mixed(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::
     const size_t bytes32 = (size_t)g.ncell * 4;
     auto residual = [&](cudaStream_t cs) {
         g.norms_async(g.ws64, 0, g.ws32.rho->p, true, cs);
-        g.mask_update_async(o.rel_tol, cs);
+        g.mask_update_async(cs);
     };
     run(g, {10, 0, 0, 0, 0}, o.use_graph, s, residual);
     check(cudaStreamSynchronize(s), "solve");

@@ -189,6 +189,8 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     d_partials = own.back()->as<double>();
     own.emplace_back(new DevBuf(sizeof(double)));
     d_scalar = own.back()->as<double>();
+    own.emplace_back(new DevBuf(sizeof(double)));
+    d_tol = own.back()->as<double>();
     check(cudaMallocHost((void **)&h_norms, 2 * T * sizeof(unsigned long long)), "cudaMallocHost");
     check(cudaMallocHost((void **)&h_nactive, sizeof(int)), "cudaMallocHost");
     check(cudaMallocHost((void **)&h_scalar, sizeof(double)), "cudaMallocHost");
@@ -312,8 +314,14 @@ void Grid::norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStr
           "norms to host");
 }
 
-void Grid::mask_update_async(double tol, cudaStream_t s) {
-    launch_mask_update(s, d_norms, T, tol, d_converged_mask(), d_nactive);
+void Grid::set_tol(double tol, cudaStream_t s) {
+    *h_scalar = tol;
+    check(cudaMemcpyAsync(d_tol, h_scalar, sizeof(double), cudaMemcpyHostToDevice, s), "tol");
+    check(cudaStreamSynchronize(s), "tol");
+}
+
+void Grid::mask_update_async(cudaStream_t s) {
+    launch_mask_update(s, d_norms, T, d_tol, d_converged_mask(), d_nactive);
     check(cudaMemcpyAsync(h_nactive, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s), "nactive");
 }
 

@@ -102,7 +102,10 @@ class Grid {
     void restrict_all(Workspace &w, cudaStream_t s);
     // composite residual of ws64 (restriction + leaf residual), norms to host buffer (async)
     void norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s);
-    void mask_update_async(double tol, cudaStream_t s);
+    // convergence mask update against the tolerance stored in d_tol
+    void mask_update_async(cudaStream_t s);
+    double *d_tol = nullptr;
+    void set_tol(double tol, cudaStream_t s);
 
     // graphs keyed by a small tuple
     std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;

@@ -56,7 +56,9 @@ void launch_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list,
 
 // Per-tree convergence mask of a batched solve: a tree stays active while
 // max|r| > tol * max|rho|; counts the active trees.
-__global__ void k_mask_update(const unsigned long long *norms, int T, double tol, int *active, int *nactive) {
+__global__ void k_mask_update(const unsigned long long *norms, int T, const double *tolp, int *active,
+                              int *nactive) {
+    const double tol = *tolp;
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -98,7 +100,8 @@ double launch_fp64_probe(cudaStream_t s, double *scratch, int iters) {
     return 2.0 * 64.0 * (double)blocks * kThreads * iters;  // flops (FMA = 2)
 }
 
-void launch_mask_update(cudaStream_t s, const unsigned long long *norms, int T, double tol, int *active, int *nactive) {
+void launch_mask_update(cudaStream_t s, const unsigned long long *norms, int T, const double *tol, int *active,
+                        int *nactive) {
     k_mask_update<<<1, kThreads, 0, s>>>(norms, T, tol, active, nactive);
     ++g_launches;
 }

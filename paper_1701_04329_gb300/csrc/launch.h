@@ -40,7 +40,8 @@ void launch_leaf_get(const LaunchCfg &, const BoxMeta &, const int *list, int n,
 void launch_bc_restrict(const LaunchCfg &, const BoxMeta &, int b0, int n, double *bc);
 // FP64 FMA throughput probe; returns the flops of one launch (FMA = 2)
 double launch_fp64_probe(cudaStream_t s, double *scratch, int iters);
-void launch_mask_update(cudaStream_t s, const unsigned long long *norms, int T, double tol, int *active,
+// tol is read from device memory, so captured graphs do not bake it in
+void launch_mask_update(cudaStream_t s, const unsigned long long *norms, int T, const double *tol, int *active,
                         int *nactive);
 // x (double) += e (float) on leaf boxes
 void launch_mixed_update(const LaunchCfg &, const BoxMeta &, const int *list, int n, double *x, const float *e);

@@ -59,12 +59,15 @@ def test_autograd_gradient_vs_central_differences():
     e = t.export()
     vol = torch.tensor(composite.cell_volumes(3, 8, e["level"], e["children"]), device="cuda")
     ustar = torch.tensor(W.blobs3d(seed=2, uniform_level=3).rho(t.cell_centers()) * 1e-4, device="cuda")
-    opts = afgpu.default_opts(rel_tol=1e-13, max_cycles=80)
+    opts = afgpu.default_opts(rel_tol=1e-12, max_cycles=80)
+    # the adjoint's relative residual floor depends on g's dynamic range; 1e-11
+    # keeps the gradient error far below the 1e-6 of the comparison
+    adj = afgpu.default_opts(rel_tol=1e-11, max_cycles=200)
     rho = torch.tensor(rho_h, device="cuda", requires_grad=True)
     b = torch.tensor(rng.normal(scale=1e-3, size=t.n_bfaces), device="cuda", requires_grad=True)
 
     def loss(r, bb):
-        u = PoissonSolve.apply(r, bb, t, opts)
+        u = PoissonSolve.apply(r, bb, t, opts, adj)
         return 0.5 * (vol * (u - ustar) ** 2).sum()
 
     L = loss(rho, b)

@@ -106,3 +106,15 @@ def test_empty_rhs_and_errors():
         t.set_rhs(z.float())
     with pytest.raises(ValueError):
         t.set_rhs(z[:-1])
+
+
+@pytest.mark.parametrize("precision", [afgpu.AFG_FP64, afgpu.AFG_MIXED])
+def test_graph_replay_honours_a_new_tolerance(precision):
+    """Cycles replay as CUDA graphs; a later solve with a tighter tolerance must
+    not reuse the earlier one (the tolerance lives in device memory)."""
+    a, b, rho, bv = pair_from_problem(W.gauss2d())
+    load(a, b, rho, bv)
+    b.solve(afgpu.default_opts(rel_tol=1e-6, precision=precision))
+    b.set_solution(torch.zeros(len(rho), dtype=torch.float64, device="cuda"))
+    st = b.solve(afgpu.default_opts(rel_tol=1e-11, precision=precision))
+    assert st["rel_residual"] <= 1e-11
