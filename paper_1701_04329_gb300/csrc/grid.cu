@@ -169,6 +169,9 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     meta.tree = upload(tree, own);
     meta.hb = d_hb = upload(hb, own);
     meta.nbase = upload(nbase, own);
+    std::vector<double> ih2(nbox);
+    for (int b = 0; b < nbox; ++b) ih2[b] = 1.0 / (hb[b] * hb[b]);
+    meta.ih2 = upload(ih2, own);
     meta.active = nullptr;
     d_child = upload(child, own);
     d_leaves = upload(leaves, own);

@@ -34,6 +34,13 @@
 namespace afg {
 
 constexpr int kThreads = 256;
+
+// Programmatic dependent launch: every kernel lets the next launch start
+// early (pdl_trigger) and waits for its predecessors to finish and their
+// memory to be visible (pdl_wait) before reading anything a kernel wrote.
+// Box metadata is written only by host uploads, so prologues may read it.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr unsigned char BF_REFINED = 1, BF_SPECIAL = 2;
 
 struct BoxMeta {
@@ -48,6 +55,7 @@ struct BoxMeta {
     const double *bc;
     const double *hb;   // cell size of every box
     const long long *nbase;  // per side: cells of the neighbour / coarse box, or Dirichlet data offset
+    const double *ih2;       // 1/h^2 of every box (an FP64 division costs ~11 FP64-pipe instructions)
 };
 
 // Metadata of one box, prefetched into shared memory one box ahead.
@@ -58,12 +66,20 @@ struct BoxInfo {
     int b, flag, poff, parent;
 };
 
+// The activity mask is written by kernels: after pdl_wait, drop a prefetched
+// box whose tree is masked out.
+// (run by the thread that wrote I.b in info_load, so no barrier is needed)
+template <int D>
+__device__ __forceinline__ void info_mask(const BoxMeta &A, BoxInfo &I, int lt, int G) {
+    if (lt == (2 * D) % G && A.active && I.b >= 0 && !A.active[A.tree[I.b]]) I.b = -1;
+}
+
 // Loads the metadata of entry `idx` of a level range (b0 + idx) or list.
 // Threads lt, lt+G, ... of the box's group share the work; b = -1 marks an
 // empty slot (past the end, or a masked tree).
 template <int D>
 __device__ __forceinline__ void info_load(const BoxMeta &A, int idx, int n, int b0, const int *list, BoxInfo &I,
-                                          int lt, int G) {
+                                          int lt, int G, bool mask = true) {
     for (int x = lt; x <= 2 * D; x += G) {
         int b = -1;
         if (idx < n) b = list ? list[idx] : b0 + idx;
@@ -73,7 +89,7 @@ __device__ __forceinline__ void info_load(const BoxMeta &A, int idx, int n, int 
                 I.base[x] = A.nbase[b * 2 * D + x];
             }
         } else {
-            if (b >= 0 && A.active && !A.active[A.tree[b]]) b = -1;
+            if (mask && b >= 0 && A.active && !A.active[A.tree[b]]) b = -1;
             I.b = b;
             if (b >= 0) {
                 I.coff = A.coff[b];
@@ -430,11 +446,14 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
     BoxInfo *info;
     short *tix, *gt, *gs;
     carve<D, M>(smem_raw, sizeof(T) * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    pdl_trigger();
     build_tables<D, M>(tix, gt, gs, colour);
     const T inv = T(1) / T(2 * D);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
-    info_load<D>(A, base + g, n, b0, list, info[g], lt, S::G);
+    info_load<D>(A, base + g, n, b0, list, info[g], lt, S::G, false);  // static metadata: before the wait
+    pdl_wait();
+    info_mask<D>(A, info[g], lt, S::G);
     __syncthreads();
     for (; base < n; base += stride) {
         const BoxInfo &I = info[buf * S::BPC + g];
@@ -492,12 +511,15 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
     BoxInfo *info;
     short *tix, *gt, *gs;
     carve<D, M>(smem_raw, sizeof(T) * 2 * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    pdl_trigger();
     build_tables<D, M>(tix, gt, gs, -1);
     constexpr int MH = M / 2;
     constexpr int NCO = D == 2 ? MH * MH : MH * MH * MH;
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
-    info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G);
+    info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G, false);  // static metadata: before the wait
+    pdl_wait();
+    info_mask<D>(A, info[g], lt, S::G);
     __syncthreads();
     for (; base < n; base += stride) {
         const BoxInfo &I = info[buf * S::BPC + g];
@@ -525,9 +547,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
                         for (int dx = 0; dx < 2; ++dx) {
                             const int t = t0 + dx + dy * P + dz * P * P;
                             const T uc = tile[t];
-                            const T lap = (nb_sum_t<D, M, T>(tile, t) - T(2 * D) * uc) * ih2;
+                            const T lap = fma(T(-2 * D), uc, nb_sum_t<D, M, T>(tile, t));
                             su += uc;
-                            sr += R[t] - lap;
+                            sr += fma(-ih2, lap, R[t]);
                         }
                 const T w = T(1) / T(1 << D);
                 const int pi = unpack_off(I.poff, 0) + X, pj = unpack_off(I.poff, 1) + Y;
@@ -562,10 +584,13 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
     BoxInfo *info;
     short *tix, *gt, *gs;
     carve<D, M>(smem_raw, sizeof(T) * 2 * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    pdl_trigger();
     build_tables<D, M>(tix, gt, gs, -1);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
-    info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G);
+    info_load<D>(A, base + g, n, b0, nullptr, info[g], lt, S::G, false);  // static metadata: before the wait
+    pdl_wait();
+    info_mask<D>(A, info[g], lt, S::G);
     __syncthreads();
     for (; base < n; base += stride) {
         const BoxInfo &I = info[buf * S::BPC + g];
@@ -593,7 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
                 for (int x = 0; x < VEC; ++x) {
                     const int q = v * VEC + x;
                     const int t = tix[q];
-                    out[x] = R[q] + (nb_sum_t<D, M, T>(tile, t) - T(2 * D) * tile[t]) * ih2;
+                    out[x] = fma(ih2, fma(T(-2 * D), tile[t], nb_sum_t<D, M, T>(tile, t)), R[q]);
                 }
                 stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
             }
@@ -619,6 +644,8 @@ __global__ void __launch_bounds__(kThreads) k_correct(BoxMeta A, int b0, int n, 
     T *dt = reinterpret_cast<T *>(smem_raw) + (threadIdx.x / Gm::G) * QC;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
     auto di = [](int x, int y, int z) { return D == 2 ? (y + 1) * Q + (x + 1) : ((z + 1) * Q + (y + 1)) * Q + (x + 1); };
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int b = resolve_box<D, M>(A, base + g, n, b0, nullptr);
         if (b >= 0) {
@@ -681,6 +708,8 @@ __global__ void __launch_bounds__(kThreads) k_restrict_u(BoxMeta A, int b0, int 
     constexpr int MH = M / 2;
     constexpr int NCO = D == 2 ? MH * MH : MH * MH * MH;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int b = resolve_box<D, M>(A, base + g, n, b0, nullptr);
         if (b < 0) continue;
@@ -698,6 +727,12 @@ __global__ void __launch_bounds__(kThreads) k_restrict_u(BoxMeta A, int b0, int 
         }
     }
 }
+
+// |x| as an ordered unsigned bit pattern (sign bit cleared; integer ops only)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float x) { return abs_bits(double(x)); }
 
 // Block-wide max of per-thread values for the tree `tr` (uniform in the
 // block), then one atomic per block.  Non-negative doubles compare like their
@@ -752,10 +787,13 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
     BoxInfo *info;
     short *tix, *gt, *gs;
     carve<D, M>(smem_raw, sizeof(T) * 2 * Gm::PC * S::BPC, S::BPC, info, tix, gt, gs);
+    pdl_trigger();
     build_tables<D, M>(tix, gt, gs, -1);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
-    info_load<D>(A, base + g, n, 0, list, info[g], lt, S::G);
+    info_load<D>(A, base + g, n, 0, list, info[g], lt, S::G, false);  // static metadata: before the wait
+    pdl_wait();
+    info_mask<D>(A, info[g], lt, S::G);
     __syncthreads();
     unsigned long long rm = 0, pm = 0;
     int cur = -1;  // tree of the running maxima (uniform in the block)
@@ -763,11 +801,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
         const BoxInfo &I = info[buf * S::BPC + g];
         const int b = I.b;
         const bool special = b >= 0 && (I.flag & BF_SPECIAL);
-        double h = 1.0;
+        double ihb = 0.0;
         if (b >= 0) {
             gather<D, M, T, S::G>(I, u, A.bc, tile, lt, -1, true, hom, tix, gt, gs);
             stage_flat<D, M, T, S::G>(rho + I.coff, RH, lt);
-            h = A.hb[b];
+            ihb = A.ih2[b];
         }
         if (lt == 0) blk_tree[g] = b >= 0 ? A.tree[b] : -1;
         info_load<D>(A, base + stride + g, n, 0, list, info[(buf ^ 1) * S::BPC + g], lt, S::G);
@@ -789,17 +827,20 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
         if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
         __syncthreads();
         if (b >= 0) {
-            const T ih2 = T(1.0 / (h * h));
+            const T ih2 = T(ihb);
             for (int v = lt; v < Gm::C / VEC; v += S::G) {
                 R out[VEC];
 #pragma unroll
                 for (int x = 0; x < VEC; ++x) {
                     const int q = v * VEC + x;
                     const int t = tix[q];
-                    const T rr = RH[q] - (nb_sum_t<D, M, T>(tile, t) - T(2 * D) * tile[t]) * ih2;
+                    // r = rho - (sum - 2D u) / h^2 as two FMAs; |.| on the bit patterns
+                    // (integer pipe), so the FP64 pipe only sees the stencil
+                    const T lap = fma(T(-2 * D), tile[t], nb_sum_t<D, M, T>(tile, t));
+                    const T rr = fma(-ih2, lap, RH[q]);
                     out[x] = R(rr);
-                    rm = max(rm, (unsigned long long)__double_as_longlong(fabs(double(rr))));
-                    pm = max(pm, (unsigned long long)__double_as_longlong(fabs(double(RH[q]))));
+                    rm = max(rm, abs_bits(rr));
+                    pm = max(pm, abs_bits(RH[q]));
                 }
                 if (rout) {
 #pragma unroll

@@ -10,6 +10,8 @@ template <int D, int M, typename T>
 __global__ void __launch_bounds__(kThreads) k_leaf_set(BoxMeta A, const int *list, int n, const double *src, T *dst) {
     using Gm = Geo<D, M>;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int li = base + g;
         if (li >= n) continue;
@@ -25,6 +27,8 @@ template <int D, int M, typename T>
 __global__ void __launch_bounds__(kThreads) k_leaf_get(BoxMeta A, const int *list, int n, const T *src, double *dst) {
     using Gm = Geo<D, M>;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int li = base + g;
         if (li >= n) continue;
@@ -43,6 +47,8 @@ __global__ void __launch_bounds__(kThreads) k_bc_restrict(BoxMeta A, int b0, int
     constexpr int MH = M / 2;
     constexpr int NF = D == 2 ? MH : MH * MH;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int idx = base + g;
         if (idx >= n) continue;
@@ -69,6 +75,8 @@ template <int D, int M>
 __global__ void __launch_bounds__(kThreads) k_mixed_update(BoxMeta A, const int *list, int n, double *x, const float *e) {
     using Gm = Geo<D, M>;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int b = resolve_box<D, M>(A, base + g, n, 0, list);
         if (b < 0) continue;
@@ -100,6 +108,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_apply(BoxMeta A, const int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *tile = reinterpret_cast<double *>(smem_raw) + (threadIdx.x / Gm::G) * Gm::PC;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     const double c1 = D == 2 ? 1.0 : 1.25;
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int b = resolve_box<D, M>(A, base + g, n, 0, list);
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_apply(BoxMeta A, const int
         __syncthreads();
         if (b >= 0) {
             const long long cb = A.coff[b];
-            const double h = hb[b], ih2 = 1.0 / (h * h);
+            const double ih2 = A.ih2[b];
             const int po = A.poff[b];
             for (int q = lt; q < Gm::C; q += Gm::G) {
                 int i, j, k;
@@ -200,6 +210,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_db(BoxMeta A, const double
                                                          const double *lam, double *db) {
     using Gm = Geo<D, M>;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int idx = base + g;
         if (idx >= n) continue;
@@ -225,6 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf_axpbypcz(BoxMeta A, const int
                                                             double c, const double *z) {
     using Gm = Geo<D, M>;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int bi = resolve_box<D, M>(A, base + g, n, 0, list);
         if (bi < 0) continue;
@@ -243,6 +257,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf_scale(BoxMeta A, const double
                                                          double *out, const double *x, int power) {
     using Gm = Geo<D, M>;
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int bi = resolve_box<D, M>(A, base + g, n, 0, list);
         if (bi < 0) continue;
@@ -261,6 +277,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf_reduce(BoxMeta A, const int *
     using Gm = Geo<D, M>;
     __shared__ double red[kThreads];
     const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
     double acc = 0.0;
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
         const int bi = resolve_box<D, M>(A, base + g, n, 0, list);

@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(kThreads) k_smooth_v(BoxMeta A, int b0, int n,
     const T c1 = D == 2 ? T(1) : T(1.25);
     const int stride = gridDim.x * S::BPC;
     int base = blockIdx.x * S::BPC, buf = 0;
-    info_load<D>(A, base + g, n, b0, list, info[g], lt, S::G);
+    pdl_trigger();
+    info_load<D>(A, base + g, n, b0, list, info[g], lt, S::G, false);  // static metadata: before the wait
+    pdl_wait();
+    info_mask<D>(A, info[g], lt, S::G);
     __syncthreads();
     for (; base < n; base += stride) {
         const BoxInfo &I = info[buf * S::BPC + g];

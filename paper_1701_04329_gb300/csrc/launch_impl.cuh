@@ -22,6 +22,24 @@ int grid_for(K kernel, size_t smem, int work_ctas) {
     return std::max(1, std::min(work_ctas, cap));
 }
 
+// Launch with programmatic stream serialization (PDL): the kernel may start
+// while its predecessor drains; every kernel waits (griddepcontrol.wait)
+// before reading data a predecessor wrote.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <int D, int M>
 inline int work_ctas(int nbox) { return (nbox + Geo<D, M>::BPC - 1) / Geo<D, M>::BPC; }
 
@@ -33,13 +51,13 @@ void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *l
         using S = SvCfg<D, M, T>;
         const size_t smem = S::smem();
         auto k = k_smooth_v<D, M, T>;
-        k<<<grid_for(k, smem, (n + S::BPC - 1) / S::BPC), kThreads, smem, c.stream>>>(
+        launch_pdl(k, grid_for(k, smem, (n + S::BPC - 1) / S::BPC), smem, c.stream, 
             A, b0, n, list, (T *)u, (const T *)rho, T(h2), colour, hom);
     } else {
         using S = SmCfg<D, M, T>;
         const size_t smem = S::smem();
         auto k = k_smooth<D, M, T>;
-        k<<<grid_for(k, smem, (n + S::BPC - 1) / S::BPC), kThreads, smem, c.stream>>>(
+        launch_pdl(k, grid_for(k, smem, (n + S::BPC - 1) / S::BPC), smem, c.stream, 
             A, b0, n, list, (T *)u, (const T *)rho, T(h2), colour, hom);
     }
     ++g_launches;
@@ -51,7 +69,7 @@ void do_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void
     if (n <= 0) return;
     const size_t smem = FullCfg<D, M, T>::smem();
     auto k = k_resid_restrict<D, M, MP, T>;
-    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (T *)u, (T *)rho, (T *)vold,
+    launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (T *)u, (T *)rho, (T *)vold,
                                                                           T(ih2), hom);
     ++g_launches;
 }
@@ -62,7 +80,7 @@ void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, 
     if (n <= 0) return;
     const size_t smem = FullCfg<D, M, T>::smem();
     auto k = k_fas<D, M, T>;
-    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (const T *)u, (T *)rho,
+    launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (const T *)u, (T *)rho,
                                                                           (T *)vold, T(ih2), hom);
     ++g_launches;
 }
@@ -73,7 +91,7 @@ void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, co
     constexpr int Q = M / 2 + 2;
     const size_t smem = sizeof(T) * (D == 2 ? Q * Q : Q * Q * Q) * Geo<D, M>::BPC;
     auto k = k_correct<D, M, MP, T>;
-    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, b0, n, (T *)u, (const T *)vold);
+    launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (T *)u, (const T *)vold);
     ++g_launches;
 }
 
@@ -81,7 +99,7 @@ template <int D, int M, int MP, typename T>
 void do_restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u) {
     if (n <= 0) return;
     auto k = k_restrict_u<D, M, MP, T>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, b0, n, (T *)u);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, b0, n, (T *)u);
     ++g_launches;
 }
 
@@ -93,11 +111,11 @@ void do_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int
     const size_t smem = FullCfg<D, M, T>::smem();
     if (rout_f32) {
         auto k = k_leaf_residual<D, M, T, float>;
-        k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(
+        launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, 
             A, list, n, (const T *)u, (const T *)rho, hom, rmax, pmax, (float *)rout);
     } else {
         auto k = k_leaf_residual<D, M, T, double>;
-        k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(
+        launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, 
             A, list, n, (const T *)u, (const T *)rho, hom, rmax, pmax, (double *)rout);
     }
     ++g_launches;
@@ -107,7 +125,7 @@ template <int D, int M, typename T>
 void do_leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
     if (n <= 0) return;
     auto k = k_leaf_set<D, M, T>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, src, (T *)dst);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, list, n, src, (T *)dst);
     ++g_launches;
 }
 
@@ -115,7 +133,7 @@ template <int D, int M, typename T>
 void do_leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
     if (n <= 0) return;
     auto k = k_leaf_get<D, M, T>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, (const T *)src, dst);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, list, n, (const T *)src, dst);
     ++g_launches;
 }
 
@@ -123,7 +141,7 @@ template <int D, int M, int MP>
 void do_bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc) {
     if (n <= 0) return;
     auto k = k_bc_restrict<D, M, MP>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, b0, n, bc);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, b0, n, bc);
     ++g_launches;
 }
 
@@ -131,7 +149,7 @@ template <int D, int M>
 void do_mixed_update(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *x, const float *e) {
     if (n <= 0) return;
     auto k = k_mixed_update<D, M>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, x, e);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, list, n, x, e);
     ++g_launches;
 }
 
@@ -141,7 +159,7 @@ void do_adjoint_apply(const LaunchCfg &c, const BoxMeta &A, const int *child, co
     if (n <= 0) return;
     const size_t smem = sizeof(double) * Geo<D, M>::PC * Geo<D, M>::BPC;
     auto k = k_adjoint_apply<D, M>;
-    k<<<grid_for(k, smem, work_ctas<D, M>(n)), kThreads, smem, c.stream>>>(A, child, hb, list, n, lam, out);
+    launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, child, hb, list, n, lam, out);
     ++g_launches;
 }
 
@@ -150,7 +168,7 @@ void do_adjoint_db(const LaunchCfg &c, const BoxMeta &A, const double *hb, const
                    double *db) {
     if (n <= 0) return;
     auto k = k_adjoint_db<D, M>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, hb, list, n, lam, db);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, hb, list, n, lam, db);
     ++g_launches;
 }
 
@@ -159,7 +177,7 @@ void do_axpbypcz(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, d
                  const double *x, double b, const double *y, double cc, const double *z) {
     if (n <= 0) return;
     auto k = k_leaf_axpbypcz<D, M>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, list, n, out, a, x, b, y, cc, z);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, list, n, out, a, x, b, y, cc, z);
     ++g_launches;
 }
 
@@ -168,7 +186,7 @@ void do_scale(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int 
               const double *x, int power) {
     if (n <= 0) return;
     auto k = k_leaf_scale<D, M>;
-    k<<<grid_for(k, 0, work_ctas<D, M>(n)), kThreads, 0, c.stream>>>(A, hb, list, n, out, x, power);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, hb, list, n, out, x, power);
     ++g_launches;
 }
 
@@ -177,7 +195,7 @@ void do_reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, con
                int mode, double *partials, double *result) {
     auto k = k_leaf_reduce<D, M>;
     const int grid = std::min(kPartials, grid_for(k, 0, std::max(1, work_ctas<D, M>(n))));
-    k<<<grid, kThreads, 0, c.stream>>>(A, list, n, x, y, mode, partials);
+    launch_pdl(k, grid, 0, c.stream, A, list, n, x, y, mode, partials);
     k_reduce_final<<<1, kThreads, 0, c.stream>>>(partials, grid, mode, result);
     g_launches += 2;
 }
