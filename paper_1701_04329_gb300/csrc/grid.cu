@@ -258,16 +258,26 @@ void Grid::down_step(Workspace &w, int l, int hom, const int *active, cudaStream
     launch_fas(cfg(l - 1, w.fp64, s), A, vc.b0, vc.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (vc.h * vc.h), hom);
 }
 
-// FAS V-cycle (Sec. 3.2) from ltop down to the coarsest grid and back.
+void Grid::bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
+    BoxMeta A = meta;
+    A.active = active;
+    int b0[4] = {0, 0, 0, 0};
+    for (int l = lmin; l <= 1; ++l) b0[l - lmin] = L(l).b0;
+    launch_bottom(cfg(1, w.fp64, s), A, T, N, lmin, ltop, mode, w.u->p, w.rho->p, w.vold->p, o.n_down, o.n_up,
+                  o.n_base, hom, b0);
+}
+
+// FAS V-cycle (Sec. 3.2) from ltop down to the coarsest grid and back.  The
+// levels at and below the root box run in one launch (k_bottom).
 void Grid::vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
-    for (int l = ltop; l > lmin; --l) {
+    for (int l = ltop; l > 1; --l) {
         smooth(w, l, o.n_down, hom, active, s);
         down_step(w, l, hom, active, s);
     }
-    smooth(w, lmin, o.n_base, hom, active, s);
+    bottom(w, ltop < 1 ? ltop : 1, 0, o, hom, active, s);
     BoxMeta A = meta;
     A.active = active;
-    for (int l = lmin + 1; l <= ltop; ++l) {
+    for (int l = 2; l <= ltop; ++l) {
         Level &v = L(l);
         launch_correct(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p);
         smooth(w, l, o.n_up, hom, active, s);
@@ -285,7 +295,9 @@ void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t
     }
     for (int l = lmax; l > lmin; --l) down_step(w, l, hom, nullptr, s);
     const size_t es = w.fp64 ? 8 : 4;
-    for (int l = lmin; l <= lmax; ++l) {
+    // steps l = lmin..1 in one launch (every tree reaches level 1)
+    bottom(w, 1, 1, o, hom, nullptr, s);
+    for (int l = 2; l <= lmax; ++l) {
         Level &v = L(l);
         const int *active = masked ? fmg_mask(l) : nullptr;
         check(cudaMemcpyAsync((char *)w.vold->p + v.c0 * es, (char *)w.u->p + v.c0 * es, v.ncell * es,

@@ -98,6 +98,8 @@ class Grid {
     void smooth(Workspace &w, int l, int steps, int hom, const int *active, cudaStream_t s);
     void down_step(Workspace &w, int l, int hom, const int *active, cudaStream_t s);
     void vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s);
+    // levels lmin..1 (one box per tree): mode 0 V-cycle from ltop, mode 1 FMG steps lmin..1
+    void bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, const int *active, cudaStream_t s);
     void fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s);
     void restrict_all(Workspace &w, cudaStream_t s);
     // composite residual of ws64 (restriction + leaf residual), norms to host buffer (async)

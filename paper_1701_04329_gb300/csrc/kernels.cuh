@@ -538,7 +538,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
             for (int c = lt; c < NCO; c += S::G) {
                 const int X = c % MH, Y = (c / MH) % MH, Z = D == 3 ? c / (MH * MH) : 0;
                 const int t0 = ti<D, M>(2 * X, 2 * Y, D == 3 ? 2 * Z : 0);
-                T su = T(0), sr = T(0);
+                // Sum of the children's residuals: each child sees D siblings and D
+                // cells outside the 2^D block, so sum_c (A u)_c = (sum_outside - D sum_c u) / h^2.
+                T su = T(0), sro = T(0), sout = T(0);
 #pragma unroll
                 for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
 #pragma unroll
@@ -546,12 +548,15 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
 #pragma unroll
                         for (int dx = 0; dx < 2; ++dx) {
                             const int t = t0 + dx + dy * P + dz * P * P;
-                            const T uc = tile[t];
-                            const T lap = fma(T(-2 * D), uc, nb_sum_t<D, M, T>(tile, t));
-                            su += uc;
-                            sr += fma(-ih2, lap, R[t]);
+                            su += tile[t];
+                            sro += R[t];
+                            // the outside neighbour of this child along each axis
+                            sout += tile[t + (dx ? 1 : -1)];
+                            sout += tile[t + (dy ? P : -P)];
+                            if (D == 3) sout += tile[t + (dz ? P * P : -P * P)];
                         }
                 const T w = T(1) / T(1 << D);
+                const T sr = fma(-ih2, fma(T(-D), su, sout), sro);
                 const int pi = unpack_off(I.poff, 0) + X, pj = unpack_off(I.poff, 1) + Y;
                 const int pk = D == 3 ? unpack_off(I.poff, 2) + Z : 0;
                 const long long q = cp + rbi<D, MP>(pi, pj, pk);
@@ -691,10 +696,9 @@ __global__ void __launch_bounds__(kThreads) k_correct(BoxMeta A, int b0, int n, 
                 const int X = i >> 1, Y = j >> 1, Z = k >> 1;
                 const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
                 const T d0 = dt[di(X, Y, Z)], dx = dt[di(X + sx, Y, Z)], dy = dt[di(X, Y + sy, Z)];
-                T add;
-                if (D == 2) add = T(0.5) * d0 + T(0.25) * (dx + dy);
-                else add = T(0.25) * (((d0 + dx) + dy) + dt[di(X, Y, Z + sz)]);
-                u[cb + q] += add;
+                const T uo = u[cb + q];
+                if (D == 2) u[cb + q] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uo));
+                else u[cb + q] = fma(T(0.25), ((d0 + dx) + dy) + dt[di(X, Y, Z + sz)], uo);
             }
         }
         __syncthreads();

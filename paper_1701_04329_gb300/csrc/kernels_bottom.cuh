@@ -1,0 +1,275 @@
+// The bottom of the multigrid hierarchy in one launch: levels 1 (the root
+// box) and below (boxes of N/2, ..., 2 cells; arXiv:1701.04329 Sec. 3.2)
+// hold exactly one box per tree, and all their sides are domain boundaries.
+// One CTA per tree stages those boxes in shared memory (solution and copy v'
+// with a ghost layer, source term, Dirichlet face data) and runs the part of
+// the FAS V-cycle below the root -- red-black Gauss-Seidel (Sec. 3.1),
+// residual and averaging restriction, the coarse right-hand side
+// (Eq. coarse-rhs), the 2-1-1 / 1-1-1-1 correction (Eq. coarse-corr) --
+// with block barriers between the steps, then writes the boxes back.  The
+// arithmetic is that of the per-level kernels, step for step.
+//
+// mode 0: one V-cycle from level ltop (<= 1) down to the coarsest grid and
+//         back up to ltop.
+// mode 1: the FMG steps l = lmin..1: store v'_l, correct from l-1 (l > lmin),
+//         V-cycle from l.
+#pragma once
+#include "kernels.cuh"
+
+namespace afg {
+
+struct BottomLevel {
+    int M, cells, padded, faces;  // faces = 2D * M^(D-1)
+    int ou, ov, orho, obc;        // shared-memory offsets (elements)
+};
+
+// 0-based red-black storage index for a runtime box size
+__device__ __forceinline__ int rbi_rt(int D, int M, int i, int j, int k) {
+    const int H = (D == 2 ? M * M : M * M * M) / 2;
+    return ((i + j + k + D) & 1) * H + (k * M + j) * (M / 2) + (i >> 1);
+}
+
+template <int D>
+__device__ __forceinline__ int pad_idx(int M, int i, int j, int k) {  // i,j,k in [-1, M]
+    return D == 2 ? (j + 1) * (M + 2) + (i + 1) : ((k + 1) * (M + 2) + (j + 1)) * (M + 2) + (i + 1);
+}
+
+template <int D>
+__device__ __forceinline__ void cell_of(int M, int c, int &i, int &j, int &k) {
+    i = c % M;
+    j = (c / M) % M;
+    k = D == 3 ? c / (M * M) : 0;
+}
+
+// Dirichlet ghosts of one box (all sides are domain boundaries): g = 2b - u_1,
+// or -u_1 for homogeneous data.  which: the padded array (u or d).
+template <int D, typename T>
+__device__ void bt_ghosts(const BottomLevel &L, T *v, const T *bc, int hom, bool homog_field) {
+    const int M = L.M, F = D == 2 ? M : M * M;
+    for (int x = threadIdx.x; x < 2 * D * F; x += blockDim.x) {
+        const int s = x / F, f = x % F;
+        const int t1 = f % M, t2 = D == 3 ? f / M : 0;
+        int i, j, k, gi, gj, gk;
+        face_pos(D, s, (s & 1) ? M - 1 : 0, t1, t2, i, j, k);
+        face_pos(D, s, (s & 1) ? M : -1, t1, t2, gi, gj, gk);
+        const T u1 = v[pad_idx<D>(M, i, j, k)];
+        const T b = (hom || homog_field) ? T(0) : bc[s * F + f];
+        v[pad_idx<D>(M, gi, gj, gk)] = T(2) * b - u1;
+    }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T bt_nbsum(int M, const T *v, int i, int j, int k) {
+    T s = (v[pad_idx<D>(M, i - 1, j, k)] + v[pad_idx<D>(M, i + 1, j, k)]) +
+          (v[pad_idx<D>(M, i, j - 1, k)] + v[pad_idx<D>(M, i, j + 1, k)]);
+    if (D == 3) s += v[pad_idx<D>(M, i, j, k - 1)] + v[pad_idx<D>(M, i, j, k + 1)];
+    return s;
+}
+
+template <int D, typename T>
+__device__ void bt_smooth(const BottomLevel &L, T *sm, int steps, int hom) {
+    const int M = L.M;
+    T *u = sm + L.ou;
+    const T *rho = sm + L.orho, *bc = sm + L.obc;
+    const T h2 = T(1) / (T(M) * T(M)), inv = T(1) / T(2 * D);
+    for (int it = 0; it < steps; ++it)
+        for (int col = 0; col < 2; ++col) {
+            bt_ghosts<D, T>(L, u, bc, hom, false);
+            __syncthreads();
+            for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+                int i, j, k;
+                cell_of<D>(M, c, i, j, k);
+                if (((i + j + k + D) & 1) != col) continue;
+                u[pad_idx<D>(M, i, j, k)] = (bt_nbsum<D, T>(M, u, i, j, k) - h2 * rho[c]) * inv;
+            }
+            __syncthreads();
+        }
+}
+
+// residual of level L, restricted into the coarse level C (which covers the
+// same domain with half the cells), then the coarse right-hand side
+template <int D, typename T>
+__device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int hom) {
+    const int M = L.M, MC = C.M;
+    T *u = sm + L.ou;
+    const T *rho = sm + L.orho;
+    T *uc = sm + C.ou, *vc = sm + C.ov, *rc = sm + C.orho;
+    const T ih2 = T(M) * T(M), ihc2 = T(MC) * T(MC), w = T(1) / T(1 << D);
+    bt_ghosts<D, T>(L, u, sm + L.obc, hom, false);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C.cells; c += blockDim.x) {
+        int X, Y, Z;
+        cell_of<D>(MC, c, X, Y, Z);
+        T su = T(0), sro = T(0), sout = T(0);
+        for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int i = 2 * X + dx, j = 2 * Y + dy, k = D == 3 ? 2 * Z + dz : 0;
+                    su += u[pad_idx<D>(M, i, j, k)];
+                    sro += rho[(k * M + j) * M + i];
+                    sout += u[pad_idx<D>(M, i + (dx ? 1 : -1), j, k)];
+                    sout += u[pad_idx<D>(M, i, j + (dy ? 1 : -1), k)];
+                    if (D == 3) sout += u[pad_idx<D>(M, i, j, k + (dz ? 1 : -1))];
+                }
+        const T mu = su * w;
+        uc[pad_idx<D>(MC, X, Y, Z)] = mu;
+        vc[pad_idx<D>(MC, X, Y, Z)] = mu;
+        rc[c] = fma(-ih2, fma(T(-D), su, sout), sro) * w;
+    }
+    __syncthreads();
+    bt_ghosts<D, T>(C, uc, sm + C.obc, hom, false);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C.cells; c += blockDim.x) {
+        int i, j, k;
+        cell_of<D>(MC, c, i, j, k);
+        const T uu = uc[pad_idx<D>(MC, i, j, k)];
+        rc[c] = fma(ihc2, fma(T(-2 * D), uu, bt_nbsum<D, T>(MC, uc, i, j, k)), rc[c]);
+    }
+    __syncthreads();
+}
+
+// u_L += I (u_C - v'_C), 2-1-1 (2D) / 1-1-1-1 (3D); ghosts of the difference -d.
+// dc: scratch for the difference (padded, coarse size)
+template <int D, typename T>
+__device__ void bt_correct(const BottomLevel &L, const BottomLevel &C, T *sm, T *dc) {
+    const int M = L.M, MC = C.M;
+    T *u = sm + L.ou;
+    const T *uc = sm + C.ou, *vc = sm + C.ov;
+    for (int c = threadIdx.x; c < C.cells; c += blockDim.x) {
+        int i, j, k;
+        cell_of<D>(MC, c, i, j, k);
+        const int p = pad_idx<D>(MC, i, j, k);
+        dc[p] = uc[p] - vc[p];
+    }
+    __syncthreads();
+    bt_ghosts<D, T>(C, dc, nullptr, 1, true);
+    __syncthreads();
+    for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+        int i, j, k;
+        cell_of<D>(M, c, i, j, k);
+        const int X = i >> 1, Y = j >> 1, Z = k >> 1;
+        const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+        const T d0 = dc[pad_idx<D>(MC, X, Y, Z)], dx = dc[pad_idx<D>(MC, X + sx, Y, Z)];
+        const T dy = dc[pad_idx<D>(MC, X, Y + sy, Z)];
+        const int q = pad_idx<D>(M, i, j, k);
+        if (D == 2) u[q] = fma(T(0.25), dx + dy, fma(T(0.5), d0, u[q]));
+        else u[q] = fma(T(0.25), ((d0 + dx) + dy) + dc[pad_idx<D>(MC, X, Y, Z + sz)], u[q]);
+    }
+    __syncthreads();
+}
+
+template <int D, typename T>
+__device__ void bt_vcycle(const BottomLevel *Ls, int lmin, int ltop, T *sm, T *dc, int nd, int nu, int nb, int hom) {
+    for (int l = ltop; l > lmin; --l) {
+        bt_smooth<D, T>(Ls[l - lmin], sm, nd, hom);
+        bt_down<D, T>(Ls[l - lmin], Ls[l - 1 - lmin], sm, hom);
+    }
+    bt_smooth<D, T>(Ls[0], sm, nb, hom);
+    for (int l = lmin + 1; l <= ltop; ++l) {
+        bt_correct<D, T>(Ls[l - lmin], Ls[l - 1 - lmin], sm, dc);
+        bt_smooth<D, T>(Ls[l - lmin], sm, nu, hom);
+    }
+}
+
+constexpr int kBottomMaxLevels = 4;  // box sizes 16, 8, 4, 2
+
+// lvl_b0[li]: first box of level lmin + li (one box per tree, tree order)
+template <int D, typename T>
+__global__ void __launch_bounds__(kThreads) k_bottom(BoxMeta A, int ntrees, int N, int lmin, int ltop, int mode,
+                                                     T *u, T *rho, T *vold, int nd, int nu, int nb, int hom,
+                                                     int4 lvl_b0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int t = blockIdx.x;
+    BottomLevel Ls[kBottomMaxLevels];
+    const int nl = 2 - lmin;
+    int off = 0;
+    for (int li = 0; li < nl; ++li) {
+        BottomLevel &L = Ls[li];
+        L.M = 2 << li;
+        L.cells = D == 2 ? L.M * L.M : L.M * L.M * L.M;
+        L.padded = D == 2 ? (L.M + 2) * (L.M + 2) : (L.M + 2) * (L.M + 2) * (L.M + 2);
+        L.faces = 2 * D * (D == 2 ? L.M : L.M * L.M);
+        L.ou = off;
+        off += L.padded;
+        L.ov = off;
+        off += L.padded;
+        L.orho = off;
+        off += L.cells;
+        L.obc = off;
+        off += L.faces;
+    }
+    T *dc = sm + off;  // correction scratch: (N/2 + 2)^D values
+    const int b0s[4] = {lvl_b0.x, lvl_b0.y, lvl_b0.z, lvl_b0.w};
+    pdl_trigger();
+    pdl_wait();
+    if (A.active && !A.active[t]) return;  // uniform per CTA: no barrier has been passed yet
+    // stage
+    for (int li = 0; li < nl; ++li) {
+        const BottomLevel &L = Ls[li];
+        const int b = b0s[li] + t;
+        const long long cb = A.coff[b];
+        for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+            int i, j, k;
+            cell_of<D>(L.M, c, i, j, k);
+            const int q = rbi_rt(D, L.M, i, j, k);
+            sm[L.ou + pad_idx<D>(L.M, i, j, k)] = u[cb + q];
+            sm[L.ov + pad_idx<D>(L.M, i, j, k)] = vold[cb + q];
+            sm[L.orho + c] = rho[cb + q];
+        }
+        const int F = D == 2 ? L.M : L.M * L.M;
+        for (int x = threadIdx.x; x < L.faces; x += blockDim.x) {
+            const int s = x / F, f = x % F;
+            sm[L.obc + x] = hom ? T(0) : T(A.bc[A.nbase[b * 2 * D + s] + f]);
+        }
+    }
+    __syncthreads();
+    if (mode == 0) {
+        bt_vcycle<D, T>(Ls, lmin, ltop, sm, dc, nd, nu, nb, hom);
+    } else {
+        for (int l = lmin; l <= 1; ++l) {
+            const BottomLevel &L = Ls[l - lmin];
+            for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+                int i, j, k;
+                cell_of<D>(L.M, c, i, j, k);
+                const int p = pad_idx<D>(L.M, i, j, k);
+                sm[L.ov + p] = sm[L.ou + p];
+            }
+            __syncthreads();
+            if (l > lmin) {
+                // the FMG correction uses the copy stored at the start of step l-1
+                bt_correct<D, T>(L, Ls[l - 1 - lmin], sm, dc);
+            }
+            bt_vcycle<D, T>(Ls, lmin, l, sm, dc, nd, nu, nb, hom);
+        }
+    }
+    // write back
+    for (int li = 0; li < nl; ++li) {
+        const BottomLevel &L = Ls[li];
+        const int b = b0s[li] + t;
+        const long long cb = A.coff[b];
+        for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+            int i, j, k;
+            cell_of<D>(L.M, c, i, j, k);
+            const int q = rbi_rt(D, L.M, i, j, k);
+            u[cb + q] = sm[L.ou + pad_idx<D>(L.M, i, j, k)];
+            vold[cb + q] = sm[L.ov + pad_idx<D>(L.M, i, j, k)];
+            rho[cb + q] = sm[L.orho + c];
+        }
+    }
+}
+
+template <int D, typename T>
+inline size_t bottom_smem(int N) {
+    size_t n = 0;
+    for (int M = 2; M <= N; M *= 2) {
+        const size_t cells = D == 2 ? M * M : M * M * M;
+        const size_t padded = D == 2 ? (M + 2) * (M + 2) : (M + 2) * (M + 2) * (M + 2);
+        n += 2 * padded + cells + 2 * D * (D == 2 ? M : M * M);
+    }
+    const size_t h = N / 2 + 2;
+    n += D == 2 ? h * h : h * h * h;  // correction scratch
+    return n * sizeof(T);
+}
+
+}  // namespace afg

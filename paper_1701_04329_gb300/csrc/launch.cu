@@ -39,6 +39,10 @@ int occupancy(const void *kernel, size_t smem) {
 #define AFG_BY_DIM(FN, ...) \
     do { if (c.D == 2) DimOps<2>::FN(__VA_ARGS__); else DimOps<3>::FN(__VA_ARGS__); } while (0)
 
+void launch_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode, void *u,
+                   void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    AFG_BY_DIM(bottom, c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+}
 void launch_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
                    double h2, int colour, int hom) { AFG_BY_DIM(smooth, c, A, b0, n, list, u, rho, h2, colour, hom); }
 void launch_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,

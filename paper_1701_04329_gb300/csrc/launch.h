@@ -19,6 +19,11 @@ struct LaunchCfg {
 // counts launches of this library's kernels (host side)
 extern unsigned long long g_launches;
 
+// the levels at and below the root box in one launch (one CTA per tree):
+// mode 0 = V-cycle from ltop (<= 1), mode 1 = the FMG steps up to level 1;
+// lvl_b0[li] = first box of level lmin + li
+void launch_bottom(const LaunchCfg &, const BoxMeta &, int ntrees, int N, int lmin, int ltop, int mode, void *u,
+                   void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
 void launch_smooth(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u, const void *rho,
                    double h2, int colour, int hom);
 void launch_resid_restrict(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, void *rho, void *vold,

@@ -7,6 +7,7 @@
 
 #include "kernels_leaf.cuh"
 #include "kernels_smooth.cuh"
+#include "kernels_bottom.cuh"
 #include "launch.h"
 
 namespace afg {
@@ -200,6 +201,18 @@ void do_reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, con
     g_launches += 2;
 }
 
+template <int D, typename T>
+void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode, void *u,
+               void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    const size_t smem = bottom_smem<D, T>(N);
+    auto k = k_bottom<D, T>;
+    occupancy(reinterpret_cast<const void *>(k), smem);  // sets the shared-memory limit once
+    const int4 b0 = make_int4(lvl_b0[0], lvl_b0[1], lvl_b0[2], lvl_b0[3]);
+    launch_pdl(k, ntrees, smem, c.stream, A, ntrees, N, lmin, ltop, mode, (T *)u, (T *)rho, (T *)vold, nd, nu, nb,
+               hom, b0);
+    ++g_launches;
+}
+
 // ---- dispatch over the box size --------------------------------------------
 [[noreturn]] inline void bad_size(int M, int MP) {
     throw std::runtime_error("unsupported box size " + std::to_string(M) + "/" + std::to_string(MP));
@@ -234,6 +247,11 @@ void do_reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, con
 
 template <int D>
 struct DimOps {
+    static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
+                       void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+        if (c.fp64) do_bottom<D, double>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+        else do_bottom<D, float>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+    }
     static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
                        const void *rho, double h2, int colour, int hom) {
         if (c.fp64) { AFG_SWITCH_M(c.M, (do_smooth<D, MM, double>(c, A, b0, n, list, u, rho, h2, colour, hom))); }
