@@ -265,6 +265,7 @@ int adjoint_solve(Grid &g, const afg_mg_opts &o, cudaStream_t s, const double *g
     const size_t bytes = (size_t)g.ncell * 8;
     auto precond = [&](const double *in, double *out, cudaStream_t cs) {
         afg::launch_leaf_scale(g.leaf_cfg(true, cs), A, g.d_hb, L, n, g.wsadj.rho->as<double>(), in, -1);
+        g.leaf_rho_hat(g.wsadj, cs);
         check(cudaMemsetAsync(g.wsadj.u->p, 0, bytes, cs), "zero");
         g.vcycle(g.wsadj, g.lmax, mo, 1, nullptr, cs);
         afg::launch_leaf_scale(g.leaf_cfg(true, cs), A, g.d_hb, L, n, out, g.wsadj.u->as<double>(), 1);
@@ -482,6 +483,7 @@ int afg_set_rhs(afg_tree *t, const double *rho) {
     AFG_API_BEGIN
     Grid &g = grid_of(t);
     afg::launch_leaf_set(g.leaf_cfg(true, t->stream), g.meta, g.d_leaves, g.n_leaf_boxes, rho, g.ws64.rho->p);
+    g.leaf_rho_hat(g.ws64, t->stream);
     check(cudaGetLastError(), "afg_set_rhs");
     g.rhs_set = true;
     return AFG_OK;
@@ -651,6 +653,7 @@ int afg_forest_set_rhs(afg_forest *f, const double *rho) {
     AFG_API_BEGIN
     Grid &g = *f->grid;
     afg::launch_leaf_set(g.leaf_cfg(true, f->stream), g.meta, g.d_leaves, g.n_leaf_boxes, rho, g.ws64.rho->p);
+    g.leaf_rho_hat(g.ws64, f->stream);
     check(cudaGetLastError(), "afg_forest_set_rhs");
     g.rhs_set = true;
     return AFG_OK;
@@ -732,7 +735,7 @@ int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, doub
     auto launch = [&](int i) {
         if (kernel == 0) {
             auto &v = g.L(level);
-            afg::launch_smooth(g.cfg(level, fp64, s), g.meta, v.b0, v.nb, nullptr, w.u->p, w.rho->p, v.h * v.h,
+            afg::launch_smooth(g.cfg(level, fp64, s), g.meta, v.b0, v.nb, nullptr, w.u->p, w.rho->p, w.rhoh_p(), v.h * v.h,
                                i & 1, 0);
         } else if (kernel == 1) {
             auto &v = g.L(level);

@@ -221,6 +221,14 @@ void Grid::alloc_ws(Workspace &w, bool fp64) {
     check(cudaMemset(w.u->p, 0, bytes), "memset");
     check(cudaMemset(w.rho->p, 0, bytes), "memset");
     check(cudaMemset(w.vold->p, 0, bytes), "memset");
+    if (fp64) {
+        w.rhoh.reset(new DevBuf(bytes));
+        check(cudaMemset(w.rhoh->p, 0, bytes), "memset");
+    }
+}
+
+void Grid::leaf_rho_hat(Workspace &w, cudaStream_t s) {
+    if (w.rhoh) launch_rho_hat(leaf_cfg(w.fp64, s), meta, d_leaves, n_leaf_boxes, w.rho->p, w.rhoh->p);
 }
 
 void Grid::ensure_mixed() {
@@ -244,7 +252,7 @@ void Grid::smooth(Workspace &w, int l, int steps, int hom, const int *active, cu
     const LaunchCfg c = cfg(l, w.fp64, s);
     for (int it = 0; it < steps; ++it)
         for (int col = 0; col < 2; ++col)
-            launch_smooth(c, A, v.b0, v.nb, nullptr, w.u->p, w.rho->p, v.h * v.h, col, hom);
+            launch_smooth(c, A, v.b0, v.nb, nullptr, w.u->p, w.rho->p, w.rhoh_p(), v.h * v.h, col, hom);
 }
 
 // Residual on level l restricted to l-1 with v_H <- I v_h, v'_H <- v_H, then
@@ -255,7 +263,8 @@ void Grid::down_step(Workspace &w, int l, int hom, const int *active, cudaStream
     BoxMeta A = meta;
     A.active = active;
     launch_resid_restrict(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (v.h * v.h), hom);
-    launch_fas(cfg(l - 1, w.fp64, s), A, vc.b0, vc.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (vc.h * vc.h), hom);
+    launch_fas(cfg(l - 1, w.fp64, s), A, vc.b0, vc.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (vc.h * vc.h), hom,
+               w.rhoh_p());
 }
 
 void Grid::bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, const int *active, cudaStream_t s) {

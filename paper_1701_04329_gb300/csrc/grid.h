@@ -39,6 +39,8 @@ struct DevBuf {
 struct Workspace {
     bool fp64 = true;
     std::unique_ptr<DevBuf> u, rho, vold;
+    std::unique_ptr<DevBuf> rhoh;  // FP64 only: -h^2 rho / (2D), read by the half-sweep
+    void *rhoh_p() const { return rhoh ? rhoh->p : nullptr; }
 };
 
 struct MgOpts {
@@ -91,6 +93,8 @@ class Grid {
     LaunchCfg leaf_cfg(bool fp64, cudaStream_t s) const { return LaunchCfg{s, D, N, N / 2, fp64}; }
 
     void alloc_ws(Workspace &w, bool fp64);
+    // refresh rho_hat of the leaves after their source term changed
+    void leaf_rho_hat(Workspace &w, cudaStream_t s);
     void ensure_mixed();
     void ensure_adjoint();
 

@@ -435,9 +435,12 @@ __device__ __forceinline__ void carve(unsigned char *raw, size_t tiles_bytes, in
 // never writes, so one launch per half-sweep is race free.  Persistent CTAs
 // walk the level; each box's metadata is prefetched one box ahead.
 // ---------------------------------------------------------------------------
+// rho_or_hat: the source term, or (scaled = 1) the pre-scaled source
+// rho_hat = -h^2 rho / (2D), for which the update is one FMA: u = sum/(2D) + rho_hat
 template <int D, int M, typename T>
 __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, const int *list, T *u,
-                                                     const T *__restrict__ rho, T h2, int colour, int hom) {
+                                                     const T *__restrict__ rho, T h2, int colour, int hom,
+                                                     int scaled) {
     using S = SmCfg<D, M, T>;
     using Gm = Geo<D, M>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -481,7 +484,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
 #pragma unroll
                     for (int x = 0; x < S::VEC; ++x) {
                         const int t = tix[colour * S::H + v * S::VEC + x];
-                        out[x] = (nb_sum_t<D, M, T>(tile, t) - h2 * rv[it][x]) * inv;
+                        const T sum = nb_sum_t<D, M, T>(tile, t);
+                        out[x] = scaled ? fma(sum, inv, rv[it][x]) : (sum - h2 * rv[it][x]) * inv;
                     }
                     stv<T, S::VEC>(u + I.coff + colour * S::H + v * S::VEC, out);
                 }
@@ -576,9 +580,10 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
 // (rho_H already holds the restricted residual): rho_H += A_H(v_H).  Leaves
 // of the level store their copy v' = v.
 // ---------------------------------------------------------------------------
+// rhoh (may be null): also store rho_hat = chat * rho_H for the scaled smoother
 template <int D, int M, typename T>
 __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, const T *u, T *rho, T *vold, T ih2,
-                                                  int hom) {
+                                                  int hom, T *rhoh, T chat) {
     using S = FullCfg<D, M, T>;
     using Gm = Geo<D, M>;
     constexpr int VEC = vec_of<T, Gm::H>();
@@ -626,6 +631,11 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
                     out[x] = fma(ih2, fma(T(-2 * D), tile[t], nb_sum_t<D, M, T>(tile, t)), R[q]);
                 }
                 stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
+                if (rhoh) {
+#pragma unroll
+                    for (int x = 0; x < VEC; ++x) out[x] *= chat;
+                    stv<T, VEC>(rhoh + I.coff + (long long)v * VEC, out);
+                }
             }
         }
         buf ^= 1;
@@ -702,6 +712,23 @@ __global__ void __launch_bounds__(kThreads) k_correct(BoxMeta A, int b0, int n, 
             }
         }
         __syncthreads();
+    }
+}
+
+// rho_hat = -h^2 rho / (2D) on a list of boxes (after the source term changed)
+template <int D, int M, typename T>
+__global__ void __launch_bounds__(kThreads) k_rho_hat(BoxMeta A, const int *list, int n, const T *rho, T *rhoh) {
+    using Gm = Geo<D, M>;
+    const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    pdl_trigger();
+    pdl_wait();
+    for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
+        const int idx = base + g;
+        if (idx >= n) continue;
+        const int b = list[idx];
+        const long long cb = A.coff[b];
+        const T c = T(-A.hb[b] * A.hb[b] / (2 * D));
+        for (int q = lt; q < Gm::C; q += Gm::G) rhoh[cb + q] = c * rho[cb + q];
     }
 }
 

@@ -44,11 +44,16 @@ void launch_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int 
     AFG_BY_DIM(bottom, c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
 }
 void launch_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
-                   double h2, int colour, int hom) { AFG_BY_DIM(smooth, c, A, b0, n, list, u, rho, h2, colour, hom); }
+                   const void *rhoh, double h2, int colour, int hom) {
+    AFG_BY_DIM(smooth, c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
+}
+void launch_rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
+    AFG_BY_DIM(rho_hat, c, A, list, n, rho, rhoh);
+}
 void launch_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
                            double ih2, int hom) { AFG_BY_DIM(resid_restrict, c, A, b0, n, u, rho, vold, ih2, hom); }
 void launch_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold, double ih2,
-                int hom) { AFG_BY_DIM(fas, c, A, b0, n, u, rho, vold, ih2, hom); }
+                int hom, void *rhoh) { AFG_BY_DIM(fas, c, A, b0, n, u, rho, vold, ih2, hom, rhoh); }
 void launch_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     AFG_BY_DIM(correct, c, A, b0, n, u, vold);
 }

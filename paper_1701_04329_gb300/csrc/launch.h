@@ -24,12 +24,16 @@ extern unsigned long long g_launches;
 // lvl_b0[li] = first box of level lmin + li
 void launch_bottom(const LaunchCfg &, const BoxMeta &, int ntrees, int N, int lmin, int ltop, int mode, void *u,
                    void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+// rhoh (may be null): use the pre-scaled source -h^2 rho/(2D) instead of rho
 void launch_smooth(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u, const void *rho,
-                   double h2, int colour, int hom);
+                   const void *rhoh, double h2, int colour, int hom);
 void launch_resid_restrict(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, void *rho, void *vold,
                            double ih2, int hom);
+// rhoh (may be null): also store the pre-scaled coarse source
 void launch_fas(const LaunchCfg &, const BoxMeta &, int b0, int n, const void *u, void *rho, void *vold, double ih2,
-                int hom);
+                int hom, void *rhoh);
+// rhoh = -h^2 rho / (2D) on a list of boxes
+void launch_rho_hat(const LaunchCfg &, const BoxMeta &, const int *list, int n, const void *rho, void *rhoh);
 void launch_correct(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, const void *vold);
 void launch_restrict_u(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u);
 // residual rho - A u on leaf boxes (cell size from the box metadata); the

@@ -46,7 +46,7 @@ inline int work_ctas(int nbox) { return (nbox + Geo<D, M>::BPC - 1) / Geo<D, M>:
 
 template <int D, int M, typename T>
 void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
-               double h2, int colour, int hom) {
+               const void *rhoh, double h2, int colour, int hom) {
     if (n <= 0) return;
     if constexpr (SvCfg<D, M, T>::ok && sizeof(T) == 4) {  // FP64 keeps k_smooth: fewer registers, FP64-bound anyway
         using S = SvCfg<D, M, T>;
@@ -59,7 +59,7 @@ void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *l
         const size_t smem = S::smem();
         auto k = k_smooth<D, M, T>;
         launch_pdl(k, grid_for(k, smem, (n + S::BPC - 1) / S::BPC), smem, c.stream, 
-            A, b0, n, list, (T *)u, (const T *)rho, T(h2), colour, hom);
+            A, b0, n, list, (T *)u, (const T *)(rhoh ? rhoh : rho), T(h2), colour, hom, rhoh ? 1 : 0);
     }
     ++g_launches;
 }
@@ -77,12 +77,13 @@ void do_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void
 
 template <int D, int M, typename T>
 void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold, double ih2,
-            int hom) {
+            int hom, void *rhoh) {
     if (n <= 0) return;
     const size_t smem = FullCfg<D, M, T>::smem();
     auto k = k_fas<D, M, T>;
+    const T chat = T(-1.0 / (ih2 * 2 * D));  // -h^2 / (2D)
     launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (const T *)u, (T *)rho,
-                                                                          (T *)vold, T(ih2), hom);
+               (T *)vold, T(ih2), hom, (T *)rhoh, chat);
     ++g_launches;
 }
 
@@ -201,6 +202,14 @@ void do_reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, con
     g_launches += 2;
 }
 
+template <int D, int M, typename T>
+void do_rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
+    if (n <= 0) return;
+    auto k = k_rho_hat<D, M, T>;
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, list, n, (const T *)rho, (T *)rhoh);
+    ++g_launches;
+}
+
 template <int D, typename T>
 void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode, void *u,
                void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
@@ -247,15 +256,19 @@ void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin
 
 template <int D>
 struct DimOps {
+    static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_rho_hat<D, MM, double>(c, A, list, n, rho, rhoh))); }
+        else { AFG_SWITCH_M(c.M, (do_rho_hat<D, MM, float>(c, A, list, n, rho, rhoh))); }
+    }
     static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
         if (c.fp64) do_bottom<D, double>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
         else do_bottom<D, float>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
     }
     static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
-                       const void *rho, double h2, int colour, int hom) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_smooth<D, MM, double>(c, A, b0, n, list, u, rho, h2, colour, hom))); }
-        else { AFG_SWITCH_M(c.M, (do_smooth<D, MM, float>(c, A, b0, n, list, u, rho, h2, colour, hom))); }
+                       const void *rho, const void *rhoh, double h2, int colour, int hom) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_smooth<D, MM, double>(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom))); }
+        else { AFG_SWITCH_M(c.M, (do_smooth<D, MM, float>(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom))); }
     }
     static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
                                double ih2, int hom) {
@@ -263,9 +276,9 @@ struct DimOps {
         else { AFG_SWITCH_MMP(c.M, c.MP, (do_resid_restrict<D, MM, PP, float>(c, A, b0, n, u, rho, vold, ih2, hom))); }
     }
     static void fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
-                    double ih2, int hom) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_fas<D, MM, double>(c, A, b0, n, u, rho, vold, ih2, hom))); }
-        else { AFG_SWITCH_M(c.M, (do_fas<D, MM, float>(c, A, b0, n, u, rho, vold, ih2, hom))); }
+                    double ih2, int hom, void *rhoh) {
+        if (c.fp64) { AFG_SWITCH_M(c.M, (do_fas<D, MM, double>(c, A, b0, n, u, rho, vold, ih2, hom, rhoh))); }
+        else { AFG_SWITCH_M(c.M, (do_fas<D, MM, float>(c, A, b0, n, u, rho, vold, ih2, hom, rhoh))); }
     }
     static void correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
         if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, double>(c, A, b0, n, u, vold))); }
