@@ -58,7 +58,7 @@ template <int D, int M>
 __device__ __forceinline__ int hrow(int j, int k) { return (k * M + j) * (M / 2); }
 
 template <int D, int M, typename T>
-__global__ void __launch_bounds__(kThreads, 6) k_smooth_v(BoxMeta A, int b0, int n, const int *list, T *u,
+__global__ void __launch_bounds__(kThreads) k_smooth_v(BoxMeta A, int b0, int n, const int *list, T *u,
                                                        const T *__restrict__ rho, T h2, int colour, int hom) {
     using S = SvCfg<D, M, T>;
     constexpr int VEC = S::VEC, MH = S::MH, H = S::H;
