@@ -64,6 +64,7 @@ struct BoxInfo {
     long long base[6];
     int code[6];
     int b, flag, poff, parent;
+    long long pcoff;  // cells of the parent (k_correct)
 };
 
 // The activity mask is written by kernels: after pdl_wait, drop a prefetched
@@ -643,31 +644,81 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
     }
 }
 
+// Metadata for the correction: the box, its parent, and the parent's side
+// codes / neighbour offsets (the correction reads the parent's neighbours).
+template <int D>
+__device__ __forceinline__ void pinfo_load(const BoxMeta &A, int idx, int n, int b0, BoxInfo &I, int lt, int G,
+                                           bool mask) {
+    for (int x = lt; x <= 2 * D; x += G) {
+        int b = idx < n ? b0 + idx : -1;
+        if (x < 2 * D) {
+            if (b >= 0) {
+                const int p = A.parent[b];
+                I.code[x] = A.nb[p * 2 * D + x];
+                I.base[x] = A.nbase[p * 2 * D + x];
+            }
+        } else {
+            if (mask && b >= 0 && A.active && !A.active[A.tree[b]]) b = -1;
+            I.b = b;
+            if (b >= 0) {
+                I.coff = A.coff[b];
+                I.poff = A.poff[b];
+                I.parent = A.parent[b];
+                I.pcoff = A.coff[I.parent];
+            }
+        }
+    }
+}
+
+template <int D, int M>
+struct CorrCfg {
+    static constexpr int MH = M / 2, Q = MH + 2;
+    static constexpr int QC = D == 2 ? Q * Q : Q * Q * Q;
+    static constexpr int G = Geo<D, M>::G, BPC = Geo<D, M>::BPC;
+    template <typename T>
+    static constexpr size_t smem() { return sizeof(T) * QC * BPC + 2 * sizeof(BoxInfo) * BPC; }
+};
+
 // ---------------------------------------------------------------------------
 // Coarse-grid correction u_h += I_H^h (v_H - v'_H) (Eq. coarse-corr) with the
 // 2-1-1 (2D) / 1-1-1-1 (3D) prolongation (Sec. 2.5) on every box of level l.
 // The difference is staged for the box's parent region plus one layer;
 // outside the parent it comes from the parent's same-level neighbour, or is
 // -d at the domain boundary (homogeneous Dirichlet ghost of a correction).
+// The box's own values are fetched (as vectors) together with the staging.
 // ---------------------------------------------------------------------------
 template <int D, int M, int MP, typename T>
 __global__ void __launch_bounds__(kThreads) k_correct(BoxMeta A, int b0, int n, T *u, const T *__restrict__ vold) {
     using Gm = Geo<D, M>;
-    constexpr int MH = M / 2, Q = MH + 2;
-    constexpr int QC = D == 2 ? Q * Q : Q * Q * Q;
+    using S = CorrCfg<D, M>;
+    constexpr int MH = S::MH, Q = S::Q, QC = S::QC;
+    constexpr int VEC = vec_of<T, Gm::H>();
+    constexpr int NV = Gm::C / VEC;
+    constexpr int NIT = (NV + S::G - 1) / S::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *dt = reinterpret_cast<T *>(smem_raw) + (threadIdx.x / Gm::G) * QC;
-    const int lt = threadIdx.x % Gm::G, g = threadIdx.x / Gm::G;
+    const int lt = threadIdx.x % S::G, g = threadIdx.x / S::G;
+    T *dt = reinterpret_cast<T *>(smem_raw) + g * QC;
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * QC * S::BPC);
     auto di = [](int x, int y, int z) { return D == 2 ? (y + 1) * Q + (x + 1) : ((z + 1) * Q + (y + 1)) * Q + (x + 1); };
+    const int stride = gridDim.x * S::BPC;
+    int base = blockIdx.x * S::BPC, buf = 0;
     pdl_trigger();
+    pinfo_load<D>(A, base + g, n, b0, info[g], lt, S::G, false);
     pdl_wait();
-    for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
-        const int b = resolve_box<D, M>(A, base + g, n, b0, nullptr);
+    info_mask<D>(A, info[g], lt, S::G);
+    __syncthreads();
+    for (; base < n; base += stride) {
+        const BoxInfo &I = info[buf * S::BPC + g];
+        const int b = I.b;
+        T uv[NIT][VEC];
         if (b >= 0) {
-            const int p = A.parent[b], po = A.poff[b];
-            const long long cp = A.coff[p];
-            const int o[3] = {unpack_off(po, 0), unpack_off(po, 1), D == 3 ? unpack_off(po, 2) : 0};
-            for (int c = lt; c < QC; c += Gm::G) {
+#pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int v = lt + it * S::G;
+                if (v < NV) ldv<T, VEC>(u + I.coff + (long long)v * VEC, uv[it]);
+            }
+            const int o[3] = {unpack_off(I.poff, 0), unpack_off(I.poff, 1), D == 3 ? unpack_off(I.poff, 2) : 0};
+            for (int c = lt; c < QC; c += S::G) {
                 const int x = c % Q - 1, y = (c / Q) % Q - 1, z = D == 3 ? c / (Q * Q) - 1 : 0;
                 const int out = (x < 0 || x >= MH) + (y < 0 || y >= MH) + (D == 3 && (z < 0 || z >= MH));
                 if (out > 1) continue;  // corners/edges are not used
@@ -679,38 +730,46 @@ __global__ void __launch_bounds__(kThreads) k_correct(BoxMeta A, int b0, int n, 
                 }
                 T d;
                 if (side < 0) {
-                    const long long q = cp + rbi<D, MP>(pc[0], pc[1], pc[2]);
+                    const long long q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
                     d = u[q] - vold[q];
                 } else {
-                    const int code = A.nb[p * 2 * D + side];
+                    const int code = I.code[side];
                     const int a = side >> 1;
                     if (code >= 0) {
                         pc[a] = (side & 1) ? 0 : MP - 1;
-                        const long long q = A.coff[code] + rbi<D, MP>(pc[0], pc[1], pc[2]);
+                        const long long q = I.base[side] + rbi<D, MP>(pc[0], pc[1], pc[2]);
                         d = u[q] - vold[q];
                     } else {
                         pc[a] = (side & 1) ? MP - 1 : 0;
-                        const long long q = cp + rbi<D, MP>(pc[0], pc[1], pc[2]);
+                        const long long q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
                         d = -(u[q] - vold[q]);
                     }
                 }
                 dt[di(x, y, z)] = d;
             }
         }
+        pinfo_load<D>(A, base + stride + g, n, b0, info[(buf ^ 1) * S::BPC + g], lt, S::G, true);
         __syncthreads();
         if (b >= 0) {
-            const long long cb = A.coff[b];
-            for (int q = lt; q < Gm::C; q += Gm::G) {
-                int i, j, k;
-                rb_cell<D, M>(q, i, j, k);
-                const int X = i >> 1, Y = j >> 1, Z = k >> 1;
-                const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
-                const T d0 = dt[di(X, Y, Z)], dx = dt[di(X + sx, Y, Z)], dy = dt[di(X, Y + sy, Z)];
-                const T uo = u[cb + q];
-                if (D == 2) u[cb + q] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uo));
-                else u[cb + q] = fma(T(0.25), ((d0 + dx) + dy) + dt[di(X, Y, Z + sz)], uo);
+#pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int v = lt + it * S::G;
+                if (v >= NV) continue;
+                T res[VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    int i, j, k;
+                    rb_cell<D, M>(v * VEC + e, i, j, k);
+                    const int X = i >> 1, Y = j >> 1, Z = k >> 1;
+                    const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+                    const T d0 = dt[di(X, Y, Z)], dx = dt[di(X + sx, Y, Z)], dy = dt[di(X, Y + sy, Z)];
+                    if (D == 2) res[e] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uv[it][e]));
+                    else res[e] = fma(T(0.25), ((d0 + dx) + dy) + dt[di(X, Y, Z + sz)], uv[it][e]);
+                }
+                stv<T, VEC>(u + I.coff + (long long)v * VEC, res);
             }
         }
+        buf ^= 1;
         __syncthreads();
     }
 }

@@ -90,8 +90,7 @@ void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, 
 template <int D, int M, int MP, typename T>
 void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     if (n <= 0) return;
-    constexpr int Q = M / 2 + 2;
-    const size_t smem = sizeof(T) * (D == 2 ? Q * Q : Q * Q * Q) * Geo<D, M>::BPC;
+    const size_t smem = CorrCfg<D, M>::template smem<T>();
     auto k = k_correct<D, M, MP, T>;
     launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (T *)u, (const T *)vold);
     ++g_launches;
