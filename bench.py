@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="afgpu", choices=["afgpu", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--uniform-level", type=int, default=6)
+    ap.add_argument("--workload", default="twosrc3d", choices=["twosrc3d", "gauss2d", "blobs3d"],
+                    help="problem of the --solve-only mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", choices=["smooth", "resid", "correct", "leafres"],
                     help="time one kernel on a uniform tree of --uniform-level (profiling case)")
@@ -102,7 +104,8 @@ def solve_only(args):
     import torch
     from paper_1701_04329_gb300 import afgpu
     from paper_1701_04329_gb300 import workloads as W
-    p = W.twosrc3d(uniform_level=args.uniform_level)
+    p = {"twosrc3d": lambda: W.twosrc3d(uniform_level=args.uniform_level), "gauss2d": W.gauss2d,
+         "blobs3d": W.blobs3d}[args.workload]()
     t = afgpu.Tree(p.dim, p.box_n, p.max_level)
     p.build(t)
     rho_h, b_h = p.data(t)
@@ -121,7 +124,8 @@ def solve_only(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             ms.append((time.perf_counter() - t0) * 1e3)
-    print(json.dumps({"solve": args.solve_only, "ms": ms, "cycles": st["cycles"], "rel": st["rel_residual"]}))
+    print(json.dumps({"solve": args.solve_only, "workload": args.workload, "unknowns": t.n_leaf_cells, "ms": ms,
+                      "cycles": st["cycles"], "rel": st["rel_residual"]}))
 
 
 def kernel_only(args):
