@@ -1,0 +1,454 @@
+// Whole-box staging with cp.async, for the kernels that apply the full
+// 2D+1-point operator to every cell of a box (both colours): the fused
+// residual + restriction (Eq. residual, Sec. 2.5) and the FAS coarse
+// right-hand side (Eq. coarse-rhs).
+//
+// Shared-memory image of a box ("colour planes"): for colour col, the
+// half-rows Q[col][row(j,k)][h] hold the cells (i, j, k) of that colour,
+// i = 2h + ((col + j + k + D) & 1), for rows j, k in [-1, M] (the rows
+// j or k = -1, M are the y/z ghost layers), and X[side][row] holds the x-side
+// ghost of each row.  Cell (i, j, k), i in [0, M), is at
+// Q[(i + j + k + D) & 1][row(j,k)][i >> 1]; a colour half of a box in global
+// memory is exactly the interior of one plane, so every interior half-row
+// and every same-level y/z ghost half-row arrives as 16-byte cp.async copies
+// (x ghosts as scalars).  Ghosts of domain-boundary and refinement-boundary
+// faces are staged as the adjacent inner value u_1 and completed after the
+// wait (Sec. 2.4 and the default scheme of Sec. 3.3):
+//   Dirichlet:           g = 2 b - u_1
+//   refinement boundary: g = u_H/2 + c1 u_1 - (u_2 + u_t1 [+ u_t2])/4,
+//                        c1 = 1 (2D), 5/4 (3D).
+// Boxes are staged one box ahead of the one being computed (two-stage ring).
+#pragma once
+#include "kernels_smooth.cuh"
+
+namespace afg {
+
+template <int D, int M, typename T, int GT = Geo<D, M>::G>
+struct FpCfg {
+    static constexpr int VEC = 16 / (int)sizeof(T);
+    static constexpr int MH = M / 2;
+    static constexpr int ROWS = D == 2 ? (M + 2) : (M + 2) * (M + 2);
+    static constexpr int PT = ROWS * MH;   // one colour plane
+    static constexpr int XT = 2 * ROWS;    // x-side ghosts [side][row]
+    static constexpr int UB = 2 * PT + XT; // u with its ghost layer
+    static constexpr int H = Geo<D, M>::H, C = 2 * H;
+    static constexpr int NVR = MH / VEC;   // vectors per half-row
+    static constexpr int FR = D == 2 ? 1 : M;
+    static constexpr int NV = C / VEC;     // interior vectors, both colours
+    static constexpr int G = GT;           // threads per box
+    static constexpr int BPC = kThreads / G;
+    static constexpr int NXR = D == 2 ? M : M * M;  // rows per x side
+    static constexpr int NXI = 2 * NXR;
+    static constexpr int NYI = (2 * D - 2) * FR * 2 * NVR;
+    static constexpr int NGI = NXI + NYI;
+    static constexpr int NST = 2;
+    static constexpr bool ok = MH >= VEC;
+    // u image + a flat copy of C more values (rho, or u for a plain copy)
+    static constexpr int BOX = UB + C;
+    static constexpr size_t smem() { return sizeof(T) * BOX * BPC * NST + sizeof(BoxInfo) * BPC * (NST + 1); }
+};
+
+// slot of cell (i, j, k), i in [0, M), j and k in [-1, M]
+template <int D, int M, typename T>
+__device__ __forceinline__ int fp_slot(int i, int j, int k) {
+    using F = FpCfg<D, M, T>;
+    return ((i + j + k + D) & 1) * F::PT + sp_row<D, M>(j, k) * F::MH + (i >> 1);
+}
+
+// x-side ghost item -> side, row (all rows)
+template <int D, int M>
+__device__ __forceinline__ void fp_xitem(int item, int &s, int &j, int &k) {
+    constexpr int NXR = D == 2 ? M : M * M;
+    s = item / NXR;
+    const int r = item % NXR;
+    j = r % M;
+    k = D == 2 ? 0 : r / M;
+}
+
+// y/z-side ghost item -> side, colour plane, vector start, ghost / inner / mirror rows
+template <int D, int M, typename T>
+__device__ __forceinline__ void fp_yzitem(int it2, int &s, int &col, int &h0, int &jg, int &kg, int &jin, int &kin,
+                                          int &jm, int &km) {
+    using F = FpCfg<D, M, T>;
+    constexpr int PER = F::FR * F::NVR;
+    s = 2 + it2 / (2 * PER);
+    const int rem = it2 % (2 * PER);
+    col = rem / PER;
+    const int r2 = rem % PER;
+    const int fr = r2 / F::NVR;
+    h0 = (r2 % F::NVR) * F::VEC;
+    const int hi = s & 1;
+    if ((s >> 1) == 1) { kg = kin = km = D == 3 ? fr : 0; jg = hi ? M : -1; jin = hi ? M - 1 : 0; jm = hi ? 0 : M - 1; }
+    else { jg = jin = jm = fr; kg = hi ? M : -1; kin = hi ? M - 1 : 0; km = hi ? 0 : M - 1; }
+}
+
+// Issues the copies of box I into its stage: the u image with ghosts, and C
+// values from `flat` (the box's rho, or null) into the flat area.
+template <int D, int M, typename T, int GT>
+__device__ __forceinline__ void fp_issue(const BoxInfo &I, const T *u, const T *flat, T *st, int lt, bool image) {
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC, MH = F::MH, H = F::H, NVH = H / VEC;
+    const T *ub = u + I.coff;
+    T *fl = st + F::UB;
+    for (int v = lt; v < F::NV; v += F::G) {
+        if (image) {
+            const int col = v / NVH, w = v % NVH;
+            const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
+            const int j = row % M, k = D == 2 ? 0 : row / M;
+            cp_async<16>(st + col * F::PT + sp_row<D, M>(j, k) * MH + h0, ub + v * VEC);
+        }
+        if (flat) cp_async<16>(fl + v * VEC, flat + I.coff + v * VEC);
+    }
+    if (!image) return;
+    for (int item = lt; item < F::NGI; item += F::G) {
+        if (item < F::NXI) {
+            int s, j, k;
+            fp_xitem<D, M>(item, s, j, k);
+            const int colg = ((s ? M : -1) + j + k + D) & 1;  // colour of the ghost cell
+            const T *src = I.code[s] >= 0 ? u + I.base[s] + colg * H + hrow<D, M>(j, k) + (s ? 0 : MH - 1)
+                                          : ub + (1 - colg) * H + hrow<D, M>(j, k) + (s ? MH - 1 : 0);
+            cp_async<(int)sizeof(T)>(st + 2 * F::PT + s * F::ROWS + sp_row<D, M>(j, k), src);
+        } else {
+            int s, col, h0, jg, kg, jin, kin, jm, km;
+            fp_yzitem<D, M, T>(item - F::NXI, s, col, h0, jg, kg, jin, kin, jm, km);
+            const T *src = I.code[s] >= 0 ? u + I.base[s] + col * H + hrow<D, M>(jm, km) + h0
+                                          : ub + (1 - col) * H + hrow<D, M>(jin, kin) + h0;
+            cp_async<16>(st + col * F::PT + sp_row<D, M>(jg, kg) * MH + h0, src);
+        }
+    }
+}
+
+// Completes the ghosts of non-copy faces from the staged u_1 (after the wait).
+template <int D, int M, typename T, int GT>
+__device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const T *u, T *st, int lt, int hom) {
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC, MH = F::MH;
+    const T c1 = D == 2 ? T(1) : T(1.25);
+    auto at = [&](int i, int j, int k) -> T { return st[fp_slot<D, M, T>(i, j, k)]; };
+    for (int item = lt; item < F::NGI; item += F::G) {
+        if (item < F::NXI) {
+            int s, j, k;
+            fp_xitem<D, M>(item, s, j, k);
+            const int code = I.code[s];
+            if (code >= 0) continue;
+            T &gv = st[2 * F::PT + s * F::ROWS + sp_row<D, M>(j, k)];
+            const T u1 = gv;
+            if (code == -1) {
+                const T bv = hom ? T(0) : T(A.bc[I.base[s] + k * M + j]);
+                gv = T(2) * bv - u1;
+            } else {
+                const int iin = s ? M - 1 : 0, p2 = s ? M - 2 : 1;
+                const int cj = unpack_off(I.poff, 1) + (j >> 1);
+                const int ck = D == 3 ? unpack_off(I.poff, 2) + (k >> 1) : 0;
+                const T uH = u[I.base[s] + rbi<D, M>(s ? 0 : M - 1, cj, ck)];
+                T acc = at(p2, j, k) + at(iin, j ^ 1, k);
+                if (D == 3) acc += at(iin, j, k ^ 1);
+                gv = T(0.5) * uH + c1 * u1 - T(0.25) * acc;
+            }
+        } else {
+            int s, col, h0, jg, kg, jin, kin, jm, km;
+            fp_yzitem<D, M, T>(item - F::NXI, s, col, h0, jg, kg, jin, kin, jm, km);
+            const int code = I.code[s];
+            if (code >= 0) continue;
+            const int hi = s & 1, a = s >> 1;
+            T *gv = st + col * F::PT + sp_row<D, M>(jg, kg) * MH + h0;
+            const int rg = (col + jg + kg + D) & 1;  // i-parity of the plane's cells in the ghost row
+            const int p2 = hi ? M - 2 : 1;
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) {
+                const int i = 2 * (h0 + x) + rg;
+                const T u1 = gv[x];
+                if (code == -1) {
+                    const int t2 = a == 1 ? kin : jin;
+                    const T bv = hom ? T(0) : T(A.bc[I.base[s] + t2 * M + i]);
+                    gv[x] = T(2) * bv - u1;
+                } else {
+                    const int ci = unpack_off(I.poff, 0) + (i >> 1);
+                    int cj, ck;
+                    T acc;
+                    if (a == 1) {
+                        cj = hi ? 0 : M - 1;
+                        ck = D == 3 ? unpack_off(I.poff, 2) + (kin >> 1) : 0;
+                        acc = at(i, p2, kin) + at(i ^ 1, jin, kin);
+                        if (D == 3) acc += at(i, jin, kin ^ 1);
+                    } else {
+                        cj = unpack_off(I.poff, 1) + (jin >> 1);
+                        ck = hi ? 0 : M - 1;
+                        acc = at(i, jin, p2) + at(i ^ 1, jin, kin);
+                        acc += at(i, jin ^ 1, kin);
+                    }
+                    const T uH = u[I.base[s] + rbi<D, M>(ci, cj, ck)];
+                    gv[x] = T(0.5) * uH + c1 * u1 - T(0.25) * acc;
+                }
+            }
+        }
+    }
+}
+
+// For the VEC cells of colour col at half-row (j,k), h0..h0+VEC-1: their
+// values and the sums of their 2D neighbours, ((x-+x+)+(y-+y+))+(z-+z+).
+template <int D, int M, typename T>
+__device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, int h0, T *self, T *sum) {
+    using F = FpCfg<D, M, T>;
+    constexpr int VEC = F::VEC, MH = F::MH;
+    const int rowi = sp_row<D, M>(j, k);
+    const int r = (col + j + k + D) & 1;  // cells at i = 2h + r; neighbours in the other plane
+    const T *po = st + (1 - col) * F::PT + rowi * MH + h0;
+    const T *X = st + 2 * F::PT;
+    T xv[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
+    ldv<T, VEC>(st + col * F::PT + rowi * MH + h0, self);
+    ldv<T, VEC>(po, xv);
+    T extra;
+    if (r) extra = h0 + VEC < MH ? po[VEC] : X[F::ROWS + rowi];
+    else extra = h0 > 0 ? po[-1] : X[rowi];
+    ldv<T, VEC>(po - MH, ym);
+    ldv<T, VEC>(po + MH, yp);
+    if (D == 3) {
+        ldv<T, VEC>(po - (M + 2) * MH, zm);
+        ldv<T, VEC>(po + (M + 2) * MH, zp);
+    }
+#pragma unroll
+    for (int x = 0; x < VEC; ++x) {
+        const T xl = r ? xv[x] : (x ? xv[x - 1] : extra);
+        const T xr = r ? (x + 1 < VEC ? xv[x + 1] : extra) : xv[x];
+        T s = (xl + xr) + (ym[x] + yp[x]);
+        if (D == 3) s += zm[x] + zp[x];
+        sum[x] = s;
+    }
+}
+
+// Prologue and ring walk shared by the kernels below.  body(I, st, lt) is
+// called once per staged box after its ghosts are complete; want(I) says
+// whether a box needs the u image, flat(I) which array goes to the flat area
+// (or null).  pre(slots) and post(slots) run in every thread of the block
+// before and after the bodies of one step, with the metadata of the step's
+// boxes (one per group).
+template <int D, int M, typename T, int GT, typename Want, typename Flat, typename Body, typename Pre,
+          typename Post>
+__device__ __forceinline__ void fp_walk(const BoxMeta &A, int b0, int n, const int *list, const T *u, int hom,
+                                        Want want, Flat flat, Body body, Pre pre, Post post) {
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int NST = F::NST, NI = NST + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / F::G, lt = threadIdx.x % F::G;
+    T *stages = reinterpret_cast<T *>(smem_raw);
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * F::BOX * F::BPC * NST);
+    const int stride = gridDim.x * F::BPC;
+    const int first = blockIdx.x * F::BPC;
+    for (int q = 0; q < NST; ++q)  // static metadata: before the wait
+        info_load<D>(A, first + q * stride + g, n, b0, list, info[q * F::BPC + g], lt, F::G, false);
+    pdl_wait();
+    for (int q = 0; q < NST; ++q) info_mask<D>(A, info[q * F::BPC + g], lt, F::G);
+    __syncthreads();
+    auto issue = [&](int q) {
+        const BoxInfo &In = info[(q % NI) * F::BPC + g];
+        if (In.b >= 0) fp_issue<D, M, T, GT>(In, u, flat(In), stages + ((q % NST) * F::BPC + g) * F::BOX, lt, want(In));
+        cp_commit();
+    };
+    for (int q = 0; q < NST - 1; ++q) issue(q);
+    int it = 0;
+    for (int base = first; base < n; base += stride, ++it) {
+        cp_wait<NST - 2>();
+        const BoxInfo &I = info[(it % NI) * F::BPC + g];
+        const bool special = I.b >= 0 && want(I) && (I.flag & BF_SPECIAL);
+        T *st = stages + ((it % NST) * F::BPC + g) * F::BOX;
+        const int any_special = __syncthreads_or(special);  // previous stage and metadata slot are free now
+        issue(it + NST - 1);
+        info_load<D>(A, base + NST * stride + g, n, b0, list, info[((it + NST) % NI) * F::BPC + g], lt, F::G);
+        pre(&info[(it % NI) * F::BPC]);
+        if (any_special) {
+            if (special) fp_fix<D, M, T, GT>(I, A, u, st, lt, hom);
+            __syncthreads();
+        }
+        if (I.b >= 0) body(I, st, lt);
+        post(&info[(it % NI) * F::BPC]);
+    }
+    cp_wait<0>();
+}
+
+// threads per box of the restriction: one per coarse cell, at least a warp
+// (FP32); FP64 boxes take the whole block (their stages are twice as large)
+template <int D, int M, typename T>
+constexpr int rr_threads() {
+    constexpr int NCO = D == 2 ? (M / 2) * (M / 2) : (M / 2) * (M / 2) * (M / 2);
+    return sizeof(T) == 8 ? Geo<D, M>::G : (NCO < 32 ? 32 : (NCO > kThreads ? kThreads : NCO));
+}
+
+// threads per box of the FAS kernel: one per interior vector, at least a warp
+template <int D, int M, typename T>
+constexpr int fas_threads() {
+    constexpr int NV = Geo<D, M>::C * (int)sizeof(T) / 16;
+    return NV < 32 ? 32 : (NV > kThreads ? kThreads : NV);
+}
+
+// Fused residual + restriction, staged version of k_resid_restrict (same
+// arithmetic and summation order).
+template <int D, int M, int MP, typename T>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict_p(BoxMeta A, int b0, int n, T *u, T *rho, T *vold,
+                                                               T ih2, int hom) {
+    constexpr int GT = rr_threads<D, M, T>();
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int MH = M / 2;
+    constexpr int NCO = D == 2 ? MH * MH : MH * MH * MH;
+    pdl_trigger();
+    auto want = [](const BoxInfo &) { return true; };
+    auto flat = [&](const BoxInfo &) -> const T * { return rho; };
+    auto body = [&](const BoxInfo &I, const T *st, int lt) {
+        const T *X = st + 2 * F::PT, *R = st + F::UB;
+        const long long cp = A.coff[I.parent];
+        for (int c = lt; c < NCO; c += F::G) {
+            const int Xc = c % MH, Y = (c / MH) % MH, Z = D == 3 ? c / (MH * MH) : 0;
+            // sum_c (A u)_c = (sum_outside - D sum_c u) / h^2 over the 2^D children
+            T su = T(0), sro = T(0), sout = T(0);
+#pragma unroll
+            for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int i = 2 * Xc + dx, j = 2 * Y + dy, k = D == 3 ? 2 * Z + dz : 0;
+                        su += st[fp_slot<D, M, T>(i, j, k)];
+                        sro += R[rbi<D, M>(i, j, k)];
+                        const int rowi = sp_row<D, M>(j, k);
+                        T xo;
+                        if (dx) xo = Xc + 1 < MH ? st[fp_slot<D, M, T>(i + 1, j, k)] : X[F::ROWS + rowi];
+                        else xo = Xc > 0 ? st[fp_slot<D, M, T>(i - 1, j, k)] : X[rowi];
+                        sout += xo;
+                        sout += st[fp_slot<D, M, T>(i, dy ? j + 1 : j - 1, k)];
+                        if (D == 3) sout += st[fp_slot<D, M, T>(i, j, dz ? k + 1 : k - 1)];
+                    }
+            const T w = T(1) / T(1 << D);
+            const T sr = fma(-ih2, fma(T(-D), su, sout), sro);
+            const int pi = unpack_off(I.poff, 0) + Xc, pj = unpack_off(I.poff, 1) + Y;
+            const int pk = D == 3 ? unpack_off(I.poff, 2) + Z : 0;
+            const long long q = cp + rbi<D, MP>(pi, pj, pk);
+            const T mu = su * w;
+            u[q] = mu;
+            vold[q] = mu;
+            rho[q] = sr * w;
+        }
+    };
+    auto none = [](const BoxInfo *) {};
+    fp_walk<D, M, T, GT>(A, b0, n, nullptr, u, hom, want, flat, body, none, none);
+}
+
+// FAS coarse right-hand side, staged version of k_fas: refined boxes get
+// rho_H += A_H(v_H) (and rho_hat = chat rho_H when rhoh is set); leaves copy
+// v' = v.
+template <int D, int M, typename T>
+__global__ void __launch_bounds__(kThreads) k_fas_p(BoxMeta A, int b0, int n, const T *u, T *rho, T *vold, T ih2,
+                                                    int hom, T *rhoh, T chat) {
+    constexpr int GT = fas_threads<D, M, T>();
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC, NVH = F::H / VEC;
+    pdl_trigger();
+    auto want = [](const BoxInfo &I) { return (I.flag & BF_REFINED) != 0; };
+    auto flat = [&](const BoxInfo &I) -> const T * { return (I.flag & BF_REFINED) ? rho : u; };
+    auto body = [&](const BoxInfo &I, const T *st, int lt) {
+        const T *FL = st + F::UB;
+        if (!(I.flag & BF_REFINED)) {
+            for (int v = lt; v < F::NV; v += F::G) {
+                T e[VEC];
+                ldv<T, VEC>(FL + v * VEC, e);
+                stv<T, VEC>(vold + I.coff + (long long)v * VEC, e);
+            }
+            return;
+        }
+        for (int v = lt; v < F::NV; v += F::G) {
+            const int col = v / NVH, w = v % NVH;
+            const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
+            const int j = row % M, k = D == 2 ? 0 : row / M;
+            T self[VEC], sum[VEC], rv[VEC], out[VEC];
+            fp_lap_vec<D, M, T>(st, col, j, k, h0, self, sum);
+            ldv<T, VEC>(FL + v * VEC, rv);
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) out[x] = fma(ih2, fma(T(-2 * D), self[x], sum[x]), rv[x]);
+            stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
+            if (rhoh) {
+#pragma unroll
+                for (int x = 0; x < VEC; ++x) out[x] *= chat;
+                stv<T, VEC>(rhoh + I.coff + (long long)v * VEC, out);
+            }
+        }
+    };
+    auto none = [](const BoxInfo *) {};
+    fp_walk<D, M, T, GT>(A, b0, n, nullptr, u, hom, want, flat, body, none, none);
+}
+
+// Composite residual on the leaves (Eq. residual with the ghost rules of
+// Secs. 2.4 and 3.3), staged version of k_leaf_residual: per tree, the
+// maxima of |r| and |rho| over the leaf cells (as bit patterns, reduced per
+// block and committed with one atomic per block when the block moves to
+// another tree, and at the end), and optionally r cast to R in rout.
+template <int D, int M, typename T, typename R>
+__global__ void __launch_bounds__(kThreads) k_leaf_residual_p(BoxMeta A, const int *list, int n, const T *u,
+                                                              const T *__restrict__ rho, int hom,
+                                                              unsigned long long *rmax, unsigned long long *pmax,
+                                                              R *rout) {
+    constexpr int GT = fas_threads<D, M, T>();
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC, NVH = F::H / VEC;
+    __shared__ unsigned long long red[64];
+    pdl_trigger();
+    const int g = threadIdx.x / F::G;
+    unsigned long long rm = 0, pm = 0;
+    int cur = -1, tr = -1;  // tree of the running maxima, tree of this step's boxes (uniform in the block)
+    bool mixed = false;
+    auto want = [](const BoxInfo &) { return true; };
+    auto flat = [&](const BoxInfo &) -> const T * { return rho; };
+    auto pre = [&](const BoxInfo *slot) {
+        tr = -1;
+        mixed = false;
+        for (int x = 0; x < F::BPC; ++x) {
+            if (slot[x].b < 0) continue;
+            const int t = A.tree[slot[x].b];
+            if (tr < 0) tr = t;
+            else if (t != tr) mixed = true;
+        }
+        if (mixed || (tr >= 0 && cur >= 0 && tr != cur)) {
+            flush_max(rm, pm, cur, cur >= 0, rmax, pmax, red);
+            rm = pm = 0;
+            cur = -1;
+        }
+    };
+    auto body = [&](const BoxInfo &I, const T *st, int lt) {
+        const T ih2 = T(A.ih2[I.b]);
+        const T *FL = st + F::UB;
+        for (int v = lt; v < F::NV; v += F::G) {
+            const int col = v / NVH, w = v % NVH;
+            const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
+            const int j = row % M, k = D == 2 ? 0 : row / M;
+            T self[VEC], sum[VEC], rv[VEC];
+            fp_lap_vec<D, M, T>(st, col, j, k, h0, self, sum);
+            ldv<T, VEC>(FL + v * VEC, rv);
+            R out[VEC];
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) {
+                // r = rho - (sum - 2D u) / h^2 as two FMAs; |.| on the bit patterns
+                const T rr = fma(-ih2, fma(T(-2 * D), self[x], sum[x]), rv[x]);
+                out[x] = R(rr);
+                rm = max(rm, abs_bits(rr));
+                pm = max(pm, abs_bits(rv[x]));
+            }
+            if (rout) {
+#pragma unroll
+                for (int x = 0; x < VEC; ++x) rout[I.coff + (long long)v * VEC + x] = out[x];
+            }
+        }
+    };
+    auto post = [&](const BoxInfo *slot) {
+        if (mixed) {  // boxes of several trees in this step: commit each box's maxima now
+            for (int x = 0; x < F::BPC; ++x) {
+                const int t = slot[x].b >= 0 ? A.tree[slot[x].b] : -1;
+                flush_max(g == x ? rm : 0ull, g == x ? pm : 0ull, t, t >= 0, rmax, pmax, red);
+            }
+            rm = pm = 0;
+        } else if (tr >= 0) {
+            cur = tr;
+        }
+    };
+    fp_walk<D, M, T, GT>(A, 0, n, list, u, hom, want, flat, body, pre, post);
+    flush_max(rm, pm, cur, cur >= 0, rmax, pmax, red);
+}
+
+}  // namespace afg

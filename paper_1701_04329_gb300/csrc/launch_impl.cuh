@@ -7,10 +7,12 @@
 
 #include "kernels_leaf.cuh"
 #include "kernels_smooth.cuh"
+#include "kernels_full.cuh"
 #include "kernels_bottom.cuh"
 #include "launch.h"
 
 namespace afg {
+
 
 int sm_count();
 // resident CTAs per SM of a kernel for a given dynamic shared memory size (cached)
@@ -64,14 +66,25 @@ void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *l
     ++g_launches;
 }
 
+// Whole-box kernels: the cp.async-staged versions wherever a half-row holds
+// a 16-byte vector (all boxes of 8^D and 16^D cells, FP64 4^D), the
+// table-driven ones otherwise.
 template <int D, int M, int MP, typename T>
 void do_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
                        double ih2, int hom) {
     if (n <= 0) return;
-    const size_t smem = FullCfg<D, M, T>::smem();
-    auto k = k_resid_restrict<D, M, MP, T>;
-    launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (T *)u, (T *)rho, (T *)vold,
-                                                                          T(ih2), hom);
+    if constexpr (FpCfg<D, M, T>::ok) {
+        using F = FpCfg<D, M, T, rr_threads<D, M, T>()>;
+        const size_t smem = F::smem();
+        auto k = k_resid_restrict_p<D, M, MP, T>;
+        launch_pdl(k, grid_for(k, smem, (n + F::BPC - 1) / F::BPC), smem, c.stream, A, b0, n, (T *)u, (T *)rho,
+                   (T *)vold, T(ih2), hom);
+    } else {
+        const size_t smem = FullCfg<D, M, T>::smem();
+        auto k = k_resid_restrict<D, M, MP, T>;
+        launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (T *)u, (T *)rho,
+                   (T *)vold, T(ih2), hom);
+    }
     ++g_launches;
 }
 
@@ -79,11 +92,19 @@ template <int D, int M, typename T>
 void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold, double ih2,
             int hom, void *rhoh) {
     if (n <= 0) return;
-    const size_t smem = FullCfg<D, M, T>::smem();
-    auto k = k_fas<D, M, T>;
     const T chat = T(-1.0 / (ih2 * 2 * D));  // -h^2 / (2D)
-    launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (const T *)u, (T *)rho,
-               (T *)vold, T(ih2), hom, (T *)rhoh, chat);
+    if constexpr (FpCfg<D, M, T>::ok) {
+        using F = FpCfg<D, M, T, fas_threads<D, M, T>()>;
+        const size_t smem = F::smem();
+        auto k = k_fas_p<D, M, T>;
+        launch_pdl(k, grid_for(k, smem, (n + F::BPC - 1) / F::BPC), smem, c.stream, A, b0, n, (const T *)u,
+                   (T *)rho, (T *)vold, T(ih2), hom, (T *)rhoh, chat);
+    } else {
+        const size_t smem = FullCfg<D, M, T>::smem();
+        auto k = k_fas<D, M, T>;
+        launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (const T *)u, (T *)rho,
+                   (T *)vold, T(ih2), hom, (T *)rhoh, chat);
+    }
     ++g_launches;
 }
 
@@ -109,15 +130,19 @@ void do_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int
                       int hom, unsigned long long *rmax, unsigned long long *pmax, void *rout,
                       bool rout_f32) {
     if (n <= 0) return;
-    const size_t smem = FullCfg<D, M, T>::smem();
-    if (rout_f32) {
-        auto k = k_leaf_residual<D, M, T, float>;
-        launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, 
-            A, list, n, (const T *)u, (const T *)rho, hom, rmax, pmax, (float *)rout);
+    auto go = [&](auto k, size_t smem, int wc, auto *out) {
+        launch_pdl(k, grid_for(k, smem, wc), smem, c.stream, A, list, n, (const T *)u, (const T *)rho, hom, rmax,
+                   pmax, out);
+    };
+    if constexpr (FpCfg<D, M, T>::ok) {
+        using F = FpCfg<D, M, T, fas_threads<D, M, T>()>;
+        const int wc = (n + F::BPC - 1) / F::BPC;
+        if (rout_f32) go(k_leaf_residual_p<D, M, T, float>, F::smem(), wc, (float *)rout);
+        else go(k_leaf_residual_p<D, M, T, double>, F::smem(), wc, (double *)rout);
     } else {
-        auto k = k_leaf_residual<D, M, T, double>;
-        launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, 
-            A, list, n, (const T *)u, (const T *)rho, hom, rmax, pmax, (double *)rout);
+        const size_t smem = FullCfg<D, M, T>::smem();
+        if (rout_f32) go(k_leaf_residual<D, M, T, float>, smem, work_ctas<D, M>(n), (float *)rout);
+        else go(k_leaf_residual<D, M, T, double>, smem, work_ctas<D, M>(n), (double *)rout);
     }
     ++g_launches;
 }
