@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="afgpu", choices=["afgpu", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--uniform-level", type=int, default=6)
+    ap.add_argument("--inner", type=int, default=None, help="FP32 V-cycles per FP64 residual (mixed solves)")
     ap.add_argument("--workload", default="twosrc3d", choices=["twosrc3d", "gauss2d", "blobs3d"],
                     help="problem of the --solve-only mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -113,6 +114,8 @@ def solve_only(args):
     zero = torch.zeros_like(rho)
     prec = afgpu.AFG_MIXED if args.solve_only == "mixed" else afgpu.AFG_FP64
     opts = afgpu.default_opts(rel_tol=args.tol, precision=prec)
+    if args.inner:
+        opts.inner_vcycles = args.inner
     t.set_rhs(rho)
     t.set_dirichlet(bv)
     ms = []

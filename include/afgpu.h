@@ -61,7 +61,9 @@ typedef struct {
     int max_cycles;    /* cycle limit for afg_solve / adjoint iterations (default 50) */
     double rel_tol;    /* stop when max|rho - A u| / max|rho| <= rel_tol (default 1e-10) */
     int precision;     /* AFG_FP64 or AFG_MIXED */
-    int inner_vcycles; /* AFG_MIXED: FP32 V-cycles per outer FP64 step (default 1) */
+    int inner_vcycles; /* AFG_MIXED: FP32 V-cycles per outer FP64 step after the first (FMG) step
+                          (default 2: each FP64 residual pass, FP64-arithmetic bound, then buys two
+                          V-cycles of reduction; 1 gives the plain alternation) */
     int use_graph;     /* 1: replay the cycle as a CUDA graph (default 1) */
 } afg_mg_opts;
 

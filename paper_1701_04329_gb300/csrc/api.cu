@@ -344,7 +344,7 @@ void afg_default_opts(afg_mg_opts *o) {
     o->max_cycles = 50;
     o->rel_tol = 1e-10;
     o->precision = AFG_FP64;
-    o->inner_vcycles = 1;
+    o->inner_vcycles = 2;
     o->use_graph = 1;
 }
 

@@ -175,6 +175,22 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     meta.active = nullptr;
     d_child = upload(child, own);
     d_leaves = upload(leaves, own);
+    // boxes (level >= 2) whose parent has a same-level leaf across a face
+    std::vector<int> cfc;
+    for (auto &v : lv) {
+        if (v.l < 2) continue;
+        for (int g = v.b0; g < v.b0 + v.nb; ++g) {
+            const int p = parent[g];
+            bool faces_leaf = false;
+            for (int s = 0; s < S; ++s) {
+                const int q = nb[p * S + s];
+                if (q >= 0 && !(bflag[q] & BF_REFINED)) faces_leaf = true;
+            }
+            if (faces_leaf) cfc.push_back(g);
+        }
+    }
+    n_cf_children = (int)cfc.size();
+    d_cf_children = cfc.empty() ? nullptr : upload(cfc, own);
     own.emplace_back(new DevBuf(std::max<long long>(1, nbc) * sizeof(double)));
     d_bc = own.back()->as<double>();
     check(cudaMemset(d_bc, 0, std::max<long long>(1, nbc) * sizeof(double)), "memset bc");
@@ -300,7 +316,7 @@ void Grid::vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *a
 void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s) {
     for (int l = lmax; l > lmin; --l) {
         Level &v = L(l);
-        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, w.u->p);
+        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, nullptr, w.u->p);
     }
     for (int l = lmax; l > lmin; --l) down_step(w, l, hom, nullptr, s);
     const size_t es = w.fp64 ? 8 : 4;
@@ -325,12 +341,19 @@ void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t
 void Grid::restrict_all(Workspace &w, cudaStream_t s) {
     for (int l = lmax; l >= 2; --l) {
         Level &v = L(l);
-        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, w.u->p);
+        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, nullptr, w.u->p);
     }
 }
 
+// The composite residual reads a parent's values only where the parent
+// faces a same-level leaf; by 2:1 balance the children of such a parent are
+// leaves, so one pass over their list restricts everything it reads.
+void Grid::restrict_cf(Workspace &w, cudaStream_t s) {
+    if (n_cf_children > 0) launch_restrict_u(cfg(2, w.fp64, s), meta, 0, n_cf_children, d_cf_children, w.u->p);
+}
+
 void Grid::norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s) {
-    restrict_all(w, s);
+    restrict_cf(w, s);
     check(cudaMemsetAsync(d_norms, 0, 2 * T * sizeof(unsigned long long), s), "memset norms");
     launch_leaf_residual(leaf_cfg(w.fp64, s), meta, d_leaves, n_leaf_boxes, w.u->p, w.rho->p, hom, d_norms,
                          d_norms + T, rout, rout_f32);

@@ -70,6 +70,8 @@ class Grid {
 
     BoxMeta meta{};  // active = nullptr
     int *d_leaves = nullptr;  // all leaf boxes, canonical (tree-major) order
+    int *d_cf_children = nullptr;  // children of parents that face a same-level leaf
+    int n_cf_children = 0;
     int *d_child = nullptr;
     double *d_hb = nullptr;
     double *d_bc = nullptr;
@@ -106,6 +108,7 @@ class Grid {
     void bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, const int *active, cudaStream_t s);
     void fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s);
     void restrict_all(Workspace &w, cudaStream_t s);
+    void restrict_cf(Workspace &w, cudaStream_t s);  // only what the composite residual reads
     // composite residual of ws64 (restriction + leaf residual), norms to host buffer (async)
     void norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s);
     // convergence mask update against the tolerance stored in d_tol

@@ -791,9 +791,10 @@ __global__ void __launch_bounds__(kThreads) k_rho_hat(BoxMeta A, const int *list
     }
 }
 
-// Restriction of u alone (FMG start, composite residual): parent region = mean of the children.
+// Restriction of u alone (FMG start, composite residual): parent region =
+// mean of the children, for the boxes b0..b0+n-1 or the n boxes of list.
 template <int D, int M, int MP, typename T>
-__global__ void __launch_bounds__(kThreads) k_restrict_u(BoxMeta A, int b0, int n, T *u) {
+__global__ void __launch_bounds__(kThreads) k_restrict_u(BoxMeta A, int b0, int n, const int *list, T *u) {
     using Gm = Geo<D, M>;
     constexpr int MH = M / 2;
     constexpr int NCO = D == 2 ? MH * MH : MH * MH * MH;
@@ -801,7 +802,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict_u(BoxMeta A, int b0, int 
     pdl_trigger();
     pdl_wait();
     for (int base = blockIdx.x * Gm::BPC; base < n; base += gridDim.x * Gm::BPC) {
-        const int b = resolve_box<D, M>(A, base + g, n, b0, nullptr);
+        const int b = resolve_box<D, M>(A, base + g, n, b0, list);
         if (b < 0) continue;
         const long long cb = A.coff[b], cp = A.coff[A.parent[b]];
         const int po = A.poff[b];

@@ -57,7 +57,9 @@ void launch_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void 
 void launch_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     AFG_BY_DIM(correct, c, A, b0, n, u, vold);
 }
-void launch_restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u) { AFG_BY_DIM(restrict_u, c, A, b0, n, u); }
+void launch_restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
+    AFG_BY_DIM(restrict_u, c, A, b0, n, list, u);
+}
 void launch_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u, const void *rho,
                           int hom, unsigned long long *rmax, unsigned long long *pmax, void *rout, bool rout_f32) {
     AFG_BY_DIM(leaf_residual, c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);

@@ -35,7 +35,8 @@ void launch_fas(const LaunchCfg &, const BoxMeta &, int b0, int n, const void *u
 // rhoh = -h^2 rho / (2D) on a list of boxes
 void launch_rho_hat(const LaunchCfg &, const BoxMeta &, const int *list, int n, const void *rho, void *rhoh);
 void launch_correct(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, const void *vold);
-void launch_restrict_u(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u);
+// boxes b0..b0+n-1, or the n boxes of list (list != nullptr)
+void launch_restrict_u(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u);
 // residual rho - A u on leaf boxes (cell size from the box metadata); the
 // residual is also stored into rout (float* when rout_f32, else double*) if
 // rout is not null

@@ -118,10 +118,10 @@ void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, co
 }
 
 template <int D, int M, int MP, typename T>
-void do_restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u) {
+void do_restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
     if (n <= 0) return;
     auto k = k_restrict_u<D, M, MP, T>;
-    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, b0, n, (T *)u);
+    launch_pdl(k, grid_for(k, 0, work_ctas<D, M>(n)), 0, c.stream, A, b0, n, list, (T *)u);
     ++g_launches;
 }
 
@@ -308,9 +308,9 @@ struct DimOps {
         if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, double>(c, A, b0, n, u, vold))); }
         else { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, float>(c, A, b0, n, u, vold))); }
     }
-    static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u) {
-        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, double>(c, A, b0, n, u))); }
-        else { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, float>(c, A, b0, n, u))); }
+    static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
+        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, double>(c, A, b0, n, list, u))); }
+        else { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, float>(c, A, b0, n, list, u))); }
     }
     static void leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
                               const void *rho, int hom, unsigned long long *rmax,
