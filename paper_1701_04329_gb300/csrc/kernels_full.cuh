@@ -451,4 +451,154 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual_p(BoxMeta A, const i
     flush_max(rm, pm, cur, cur >= 0, rmax, pmax, red);
 }
 
+// ---------------------------------------------------------------------------
+// Coarse-grid correction u_h += I_H^h (v_H - v'_H) (Eq. coarse-corr), staged
+// version of k_correct: a box's own values (16-byte copies) and the parent's
+// v_H and v'_H over the box's parent region plus one layer (scalar copies;
+// outside the parent from its same-level neighbour, or mirrored inside it at
+// the domain boundary, where the difference changes sign) arrive by cp.async
+// one box ahead; d = v_H - v'_H is formed once per staged value, then the
+// 2-1-1 / 1-1-1-1 prolongation (Sec. 2.5) is added.
+// ---------------------------------------------------------------------------
+template <int D, int M, typename T>
+struct CpCfg {
+    static constexpr int MH = M / 2, Q = MH + 2;
+    static constexpr int QC = D == 2 ? Q * Q : Q * Q * Q;
+    static constexpr int VEC = 16 / (int)sizeof(T);
+    static constexpr int QCP = (QC + VEC - 1) / VEC * VEC;  // keeps 16-byte alignment
+    static constexpr int C = Geo<D, M>::C;
+    static constexpr int NV = C / VEC;
+    static constexpr int G = NV < kThreads ? NV : kThreads;
+    static constexpr int BPC = kThreads / G;
+    static constexpr int NIT = (NV + G - 1) / G;
+    static constexpr int BOX = C + 2 * QCP;
+    static constexpr int NST = 2;
+    static constexpr bool ok = MH >= VEC;  // a vector stays inside one half-row
+    static constexpr size_t smem() { return sizeof(T) * BOX * BPC * NST + sizeof(BoxInfo) * BPC * (NST + 1); }
+};
+
+// padded parent-region slot c -> (x, y, z) in [-1, MH], side of the parent it
+// lies beyond (-1: inside), and whether it is used (corners/edges are not)
+template <int D, int M>
+__device__ __forceinline__ bool cp_slot(int c, int &x, int &y, int &z) {
+    constexpr int Q = M / 2 + 2, MH = M / 2;
+    x = c % Q - 1;
+    y = (c / Q) % Q - 1;
+    z = D == 3 ? c / (Q * Q) - 1 : 0;
+    const int out = (x < 0 || x >= MH) + (y < 0 || y >= MH) + (D == 3 && (z < 0 || z >= MH));
+    return out <= 1;
+}
+
+template <int D, int M, int MP>
+__device__ __forceinline__ int cp_side(const BoxInfo &I, int x, int y, int z, int (&pc)[3]) {
+    pc[0] = unpack_off(I.poff, 0) + x;
+    pc[1] = unpack_off(I.poff, 1) + y;
+    pc[2] = D == 3 ? unpack_off(I.poff, 2) + z : 0;
+    int side = -1;
+    for (int a = 0; a < D; ++a) {
+        if (pc[a] < 0) side = 2 * a;
+        else if (pc[a] >= MP) side = 2 * a + 1;
+    }
+    return side;
+}
+
+template <int D, int M, int MP, typename T>
+__device__ __forceinline__ void cp_issue(const BoxInfo &I, const T *u, const T *vold, T *st, int lt) {
+    using S = CpCfg<D, M, T>;
+    T *U = st, *DU = st + S::C, *DV = DU + S::QCP;
+    for (int v = lt; v < S::NV; v += S::G) cp_async<16>(U + v * S::VEC, u + I.coff + (long long)v * S::VEC);
+    for (int c = lt; c < S::QC; c += S::G) {
+        int x, y, z;
+        if (!cp_slot<D, M>(c, x, y, z)) continue;
+        int pc[3];
+        const int side = cp_side<D, M, MP>(I, x, y, z, pc);
+        long long q;
+        if (side < 0) {
+            q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
+        } else {
+            const int a = side >> 1;
+            if (I.code[side] >= 0) {
+                pc[a] = (side & 1) ? 0 : MP - 1;
+                q = I.base[side] + rbi<D, MP>(pc[0], pc[1], pc[2]);
+            } else {  // domain boundary: the mirrored cell (a refined box has no coarser neighbour)
+                pc[a] = (side & 1) ? MP - 1 : 0;
+                q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
+            }
+        }
+        cp_async<(int)sizeof(T)>(DU + c, u + q);
+        cp_async<(int)sizeof(T)>(DV + c, vold + q);
+    }
+}
+
+template <int D, int M, int MP, typename T>
+__global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n, T *u, const T *__restrict__ vold) {
+    using S = CpCfg<D, M, T>;
+    constexpr int NST = S::NST, NI = NST + 1, Q = S::Q, VEC = S::VEC, MH = S::MH;
+    constexpr int NVH = Geo<D, M>::H / VEC, NVR = MH / VEC > 0 ? MH / VEC : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
+    T *stages = reinterpret_cast<T *>(smem_raw);
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * S::BOX * S::BPC * NST);
+    const int stride = gridDim.x * S::BPC;
+    const int first = blockIdx.x * S::BPC;
+    pdl_trigger();
+    for (int q = 0; q < NST; ++q)  // static metadata: before the wait
+        pinfo_load<D>(A, first + q * stride + g, n, b0, info[q * S::BPC + g], lt, S::G, false);
+    pdl_wait();
+    for (int q = 0; q < NST; ++q) info_mask<D>(A, info[q * S::BPC + g], lt, S::G);
+    __syncthreads();
+    auto issue = [&](int q) {
+        const BoxInfo &In = info[(q % NI) * S::BPC + g];
+        if (In.b >= 0) cp_issue<D, M, MP, T>(In, u, vold, stages + ((q % NST) * S::BPC + g) * S::BOX, lt);
+        cp_commit();
+    };
+    for (int q = 0; q < NST - 1; ++q) issue(q);
+    int it = 0;
+    for (int base = first; base < n; base += stride, ++it) {
+        cp_wait<NST - 2>();
+        __syncthreads();  // this box's copies are visible; the previous stage and metadata slot are free
+        const BoxInfo &I = info[(it % NI) * S::BPC + g];
+        T *st = stages + ((it % NST) * S::BPC + g) * S::BOX;
+        issue(it + NST - 1);
+        pinfo_load<D>(A, base + NST * stride + g, n, b0, info[((it + NST) % NI) * S::BPC + g], lt, S::G, true);
+        T *U = st, *DU = st + S::C;
+        const T *DV = DU + S::QCP;
+        if (I.b >= 0) {  // d = v_H - v'_H in place, negated across the domain boundary
+            for (int c = lt; c < S::QC; c += S::G) {
+                int x, y, z;
+                if (!cp_slot<D, M>(c, x, y, z)) continue;
+                int pc[3];
+                const int side = cp_side<D, M, MP>(I, x, y, z, pc);
+                DU[c] = (side >= 0 && I.code[side] < 0) ? DV[c] - DU[c] : DU[c] - DV[c];
+            }
+        }
+        __syncthreads();
+        if (I.b >= 0) {
+#pragma unroll
+            for (int itv = 0; itv < S::NIT; ++itv) {
+                const int v = lt + itv * S::G;
+                if (v >= S::NV) continue;
+                // the VEC cells of a half-row vector: colour col, row (j,k), i = 2h + r for
+                // h = h0..h0+VEC-1; their coarse cells (h, j/2, k/2) and offsets are shared
+                const int col = v / NVH, w = v % NVH;
+                const int row = w / NVR, h0 = (w % NVR) * VEC;
+                const int j = row % M, k = D == 2 ? 0 : row / M;
+                const int r = (col + j + k + D) & 1;
+                const int ox = r ? 1 : -1, oy = (j & 1) ? Q : -Q, oz = (k & 1) ? Q * Q : -Q * Q;
+                const int b = D == 2 ? ((j >> 1) + 1) * Q + (h0 + 1) : (((k >> 1) + 1) * Q + ((j >> 1) + 1)) * Q + (h0 + 1);
+                T uv[VEC], res[VEC];
+                ldv<T, VEC>(U + v * VEC, uv);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const T d0 = DU[b + e], dx = DU[b + e + ox], dy = DU[b + e + oy];
+                    if (D == 2) res[e] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uv[e]));
+                    else res[e] = fma(T(0.25), ((d0 + dx) + dy) + DU[b + e + oz], uv[e]);
+                }
+                stv<T, VEC>(u + I.coff + (long long)v * VEC, res);
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
 }  // namespace afg

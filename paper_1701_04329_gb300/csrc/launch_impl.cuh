@@ -111,6 +111,16 @@ void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, 
 template <int D, int M, int MP, typename T>
 void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     if (n <= 0) return;
+    // FP32: staged copies (the FP64 correction is bound by its FP64 additions either way)
+    if constexpr (CpCfg<D, M, T>::ok && sizeof(T) == 4) {
+        using S = CpCfg<D, M, T>;
+        const size_t smem = S::smem();
+        auto k = k_correct_p<D, M, MP, T>;
+        launch_pdl(k, grid_for(k, smem, (n + S::BPC - 1) / S::BPC), smem, c.stream, A, b0, n, (T *)u,
+                   (const T *)vold);
+        ++g_launches;
+        return;
+    }
     const size_t smem = CorrCfg<D, M>::template smem<T>();
     auto k = k_correct<D, M, MP, T>;
     launch_pdl(k, grid_for(k, smem, work_ctas<D, M>(n)), smem, c.stream, A, b0, n, (T *)u, (const T *)vold);
