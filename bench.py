@@ -148,6 +148,13 @@ def kernel_only(args):
     print(json.dumps(r), flush=True)
 
 
+# DRAM bytes (read + write) per launch of the roofline kernels on the 256^3 level, from one ncu
+# capture of `bench.py --kernel-only smooth [--fp32] --reps 3` of the kernel as it is now; None
+# when that kernel has not been captured since it last changed.
+TRAFFIC = {("k_smooth<3,8,double>", 6): 197063680, ("k_smooth_p<3,8,float>", 6): 84080896}
+TRAFFIC_UNIT = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -407,14 +414,18 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_smooth<3,8,double> (half-sweep, level %d)" % lvl,
                      "achieved": ach64, "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": ach64 / fp64_peak_tflops,
                      "peak_source": "FP64 FMA probe run in this process (FMA = 2 flops)",
-                     "ms": k64["ms"], "hbm_gbs": gbs64, "hbm_frac": gbs64 / hbm, "traffic": None},
+                     "ms": k64["ms"], "hbm_gbs": gbs64, "hbm_frac": gbs64 / hbm,
+                     "traffic": TRAFFIC.get(("k_smooth<3,8,double>", lvl)), "traffic_unit": TRAFFIC_UNIT,
+                     "algorithmic_bytes": k64["bytes"]},
         "mixed": {"value": vmx, "unit": "unknowns/s", "ms_per_step": msmx, "dtype": "f32+f64",
                   "cycles": stmx["cycles"], "rel_residual": stmx["rel_residual"], "err_vs_fp64_1e-12": errmx,
                   "speedup_vs_fp64": ms64 / msmx, "gpu_launches": launches_mx,
                   "e2e": {"value": world * n / (ms_e2e_mx * 1e-3), "unit": "unknowns/s"},
-                  "roofline": {"bound": "hbm", "kernel": "k_smooth<3,8,float> (half-sweep, level %d)" % lvl,
+                  "roofline": {"bound": "hbm", "kernel": "k_smooth_p<3,8,float> (half-sweep, level %d)" % lvl,
                                "achieved": gbs32, "peak": hbm, "unit": "GB/s", "frac": gbs32 / hbm,
-                               "peak_source": pk_src + " (hbm_gbs, burst)", "ms": k32["ms"], "traffic": None}},
+                               "peak_source": pk_src + " (hbm_gbs, burst)", "ms": k32["ms"],
+                               "traffic": TRAFFIC.get(("k_smooth_p<3,8,float>", lvl)), "traffic_unit": TRAFFIC_UNIT,
+                               "algorithmic_bytes": k32["bytes"]}},
         "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": int(rho_h.nbytes + b_h.nbytes), "d2h_bytes_per_step": int(n * 8)},
         "gpu_launches": launches,

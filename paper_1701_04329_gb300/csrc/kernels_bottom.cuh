@@ -41,63 +41,74 @@ __device__ __forceinline__ void cell_of(int M, int c, int &i, int &j, int &k) {
     k = D == 3 ? c / (M * M) : 0;
 }
 
-// Dirichlet ghosts of one box (all sides are domain boundaries): g = 2b - u_1,
-// or -u_1 for homogeneous data.  which: the padded array (u or d).
-template <int D, typename T>
-__device__ void bt_ghosts(const BottomLevel &L, T *v, const T *bc, int hom, bool homog_field) {
-    const int M = L.M, F = D == 2 ? M : M * M;
-    for (int x = threadIdx.x; x < 2 * D * F; x += blockDim.x) {
-        const int s = x / F, f = x % F;
-        const int t1 = f % M, t2 = D == 3 ? f / M : 0;
-        int i, j, k, gi, gj, gk;
-        face_pos(D, s, (s & 1) ? M - 1 : 0, t1, t2, i, j, k);
-        face_pos(D, s, (s & 1) ? M : -1, t1, t2, gi, gj, gk);
-        const T u1 = v[pad_idx<D>(M, i, j, k)];
-        const T b = (hom || homog_field) ? T(0) : bc[s * F + f];
-        v[pad_idx<D>(M, gi, gj, gk)] = T(2) * b - u1;
-    }
+// c-th cell of colour col (c < M^D / 2), box size known at compile time
+template <int D, int M>
+__device__ __forceinline__ void bt_cell(int c, int col, int &i, int &j, int &k) {
+    constexpr int MH = M / 2;
+    const int h = c % MH, row = c / MH;
+    j = row % M;
+    k = D == 3 ? row / M : 0;
+    i = 2 * h + ((col + j + k + D) & 1);
 }
 
-template <int D, typename T>
-__device__ __forceinline__ T bt_nbsum(int M, const T *v, int i, int j, int k) {
-    T s = (v[pad_idx<D>(M, i - 1, j, k)] + v[pad_idx<D>(M, i + 1, j, k)]) +
-          (v[pad_idx<D>(M, i, j - 1, k)] + v[pad_idx<D>(M, i, j + 1, k)]);
-    if (D == 3) s += v[pad_idx<D>(M, i, j, k - 1)] + v[pad_idx<D>(M, i, j, k + 1)];
+// Every side of a bottom box is a domain boundary, so a neighbour outside
+// the box is the Dirichlet ghost g = 2b - u_1 whose inner cell u_1 is the
+// cell itself (b = 0 for homogeneous data).  Face data: side s, face cell
+// t2 * M + t1 with (t1, t2) the tangential coordinates, x first.
+template <int D, int M, typename T>
+__device__ __forceinline__ T bt_ghost(const T *bc, bool zero_b, int s, int t1, int t2, T self) {
+    constexpr int F = D == 2 ? M : M * M;
+    const T b = zero_b ? T(0) : bc[s * F + t2 * M + t1];
+    return T(2) * b - self;
+}
+
+// ((x- + x+) + (y- + y+)) + (z- + z+) around interior cell (i,j,k), ghosts folded in
+template <int D, int M, typename T>
+__device__ __forceinline__ T bt_sum(const T *v, const T *bc, bool zero_b, int i, int j, int k, T self) {
+    const T xm = i > 0 ? v[pad_idx<D>(M, i - 1, j, k)] : bt_ghost<D, M, T>(bc, zero_b, 0, j, k, self);
+    const T xp = i < M - 1 ? v[pad_idx<D>(M, i + 1, j, k)] : bt_ghost<D, M, T>(bc, zero_b, 1, j, k, self);
+    const T ym = j > 0 ? v[pad_idx<D>(M, i, j - 1, k)] : bt_ghost<D, M, T>(bc, zero_b, 2, i, k, self);
+    const T yp = j < M - 1 ? v[pad_idx<D>(M, i, j + 1, k)] : bt_ghost<D, M, T>(bc, zero_b, 3, i, k, self);
+    T s = (xm + xp) + (ym + yp);
+    if (D == 3) {
+        const T zm = k > 0 ? v[pad_idx<D>(M, i, j, k - 1)] : bt_ghost<D, M, T>(bc, zero_b, 4, i, j, self);
+        const T zp = k < M - 1 ? v[pad_idx<D>(M, i, j, k + 1)] : bt_ghost<D, M, T>(bc, zero_b, 5, i, j, self);
+        s += zm + zp;
+    }
     return s;
 }
 
-template <int D, typename T>
+// one barrier per half-sweep: the colour-c cells read only colour 1-c cells
+// and their own ghosts
+template <int D, int M, typename T>
 __device__ void bt_smooth(const BottomLevel &L, T *sm, int steps, int hom) {
-    const int M = L.M;
+    constexpr int H = (D == 2 ? M * M : M * M * M) / 2;
     T *u = sm + L.ou;
     const T *rho = sm + L.orho, *bc = sm + L.obc;
     const T h2 = T(1) / (T(M) * T(M)), inv = T(1) / T(2 * D);
     for (int it = 0; it < steps; ++it)
         for (int col = 0; col < 2; ++col) {
-            bt_ghosts<D, T>(L, u, bc, hom, false);
-            __syncthreads();
-            for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+            for (int c = threadIdx.x; c < H; c += blockDim.x) {
                 int i, j, k;
-                cell_of<D>(M, c, i, j, k);
-                if (((i + j + k + D) & 1) != col) continue;
-                u[pad_idx<D>(M, i, j, k)] = (bt_nbsum<D, T>(M, u, i, j, k) - h2 * rho[c]) * inv;
+                bt_cell<D, M>(c, col, i, j, k);
+                const int p = pad_idx<D>(M, i, j, k);
+                const T sum = bt_sum<D, M, T>(u, bc, hom, i, j, k, u[p]);
+                u[p] = (sum - h2 * rho[(k * M + j) * M + i]) * inv;
             }
             __syncthreads();
         }
 }
 
-// residual of level L, restricted into the coarse level C (which covers the
-// same domain with half the cells), then the coarse right-hand side
-template <int D, typename T>
+// residual of level L (box size M), restricted into the coarse level C (M/2,
+// same domain), then the coarse right-hand side
+template <int D, int M, typename T>
 __device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int hom) {
-    const int M = L.M, MC = C.M;
-    T *u = sm + L.ou;
+    constexpr int MC = M / 2, CC = D == 2 ? MC * MC : MC * MC * MC;
+    const T *u = sm + L.ou, *bcf = sm + L.obc;
     const T *rho = sm + L.orho;
     T *uc = sm + C.ou, *vc = sm + C.ov, *rc = sm + C.orho;
     const T ih2 = T(M) * T(M), ihc2 = T(MC) * T(MC), w = T(1) / T(1 << D);
-    bt_ghosts<D, T>(L, u, sm + L.obc, hom, false);
-    __syncthreads();
-    for (int c = threadIdx.x; c < C.cells; c += blockDim.x) {
+    for (int c = threadIdx.x; c < CC; c += blockDim.x) {
         int X, Y, Z;
         cell_of<D>(MC, c, X, Y, Z);
         T su = T(0), sro = T(0), sout = T(0);
@@ -105,11 +116,17 @@ __device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int h
             for (int dy = 0; dy < 2; ++dy)
                 for (int dx = 0; dx < 2; ++dx) {
                     const int i = 2 * X + dx, j = 2 * Y + dy, k = D == 3 ? 2 * Z + dz : 0;
-                    su += u[pad_idx<D>(M, i, j, k)];
+                    const T uu = u[pad_idx<D>(M, i, j, k)];
+                    su += uu;
                     sro += rho[(k * M + j) * M + i];
-                    sout += u[pad_idx<D>(M, i + (dx ? 1 : -1), j, k)];
-                    sout += u[pad_idx<D>(M, i, j + (dy ? 1 : -1), k)];
-                    if (D == 3) sout += u[pad_idx<D>(M, i, j, k + (dz ? 1 : -1))];
+                    const int io = i + (dx ? 1 : -1), jo = j + (dy ? 1 : -1), ko = k + (dz ? 1 : -1);
+                    sout += (io >= 0 && io < M) ? u[pad_idx<D>(M, io, j, k)]
+                                                : bt_ghost<D, M, T>(bcf, hom, dx, j, k, uu);
+                    sout += (jo >= 0 && jo < M) ? u[pad_idx<D>(M, i, jo, k)]
+                                                : bt_ghost<D, M, T>(bcf, hom, 2 + dy, i, k, uu);
+                    if (D == 3)
+                        sout += (ko >= 0 && ko < M) ? u[pad_idx<D>(M, i, j, ko)]
+                                                    : bt_ghost<D, M, T>(bcf, hom, 4 + dz, i, j, uu);
                 }
         const T mu = su * w;
         uc[pad_idx<D>(MC, X, Y, Z)] = mu;
@@ -117,57 +134,70 @@ __device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int h
         rc[c] = fma(-ih2, fma(T(-D), su, sout), sro) * w;
     }
     __syncthreads();
-    bt_ghosts<D, T>(C, uc, sm + C.obc, hom, false);
-    __syncthreads();
-    for (int c = threadIdx.x; c < C.cells; c += blockDim.x) {
+    for (int c = threadIdx.x; c < CC; c += blockDim.x) {
         int i, j, k;
         cell_of<D>(MC, c, i, j, k);
         const T uu = uc[pad_idx<D>(MC, i, j, k)];
-        rc[c] = fma(ihc2, fma(T(-2 * D), uu, bt_nbsum<D, T>(MC, uc, i, j, k)), rc[c]);
+        rc[c] = fma(ihc2, fma(T(-2 * D), uu, bt_sum<D, MC, T>(uc, sm + C.obc, hom, i, j, k, uu)), rc[c]);
     }
     __syncthreads();
 }
 
-// u_L += I (u_C - v'_C), 2-1-1 (2D) / 1-1-1-1 (3D); ghosts of the difference -d.
+// u_L += I (u_C - v'_C), 2-1-1 (2D) / 1-1-1-1 (3D); outside the box the
+// difference is -d of the cell inside (homogeneous Dirichlet ghost).
 // dc: scratch for the difference (padded, coarse size)
-template <int D, typename T>
+template <int D, int M, typename T>
 __device__ void bt_correct(const BottomLevel &L, const BottomLevel &C, T *sm, T *dc) {
-    const int M = L.M, MC = C.M;
+    constexpr int MC = M / 2, CC = D == 2 ? MC * MC : MC * MC * MC, CL = D == 2 ? M * M : M * M * M;
     T *u = sm + L.ou;
     const T *uc = sm + C.ou, *vc = sm + C.ov;
-    for (int c = threadIdx.x; c < C.cells; c += blockDim.x) {
+    for (int c = threadIdx.x; c < CC; c += blockDim.x) {
         int i, j, k;
         cell_of<D>(MC, c, i, j, k);
         const int p = pad_idx<D>(MC, i, j, k);
         dc[p] = uc[p] - vc[p];
     }
     __syncthreads();
-    bt_ghosts<D, T>(C, dc, nullptr, 1, true);
-    __syncthreads();
-    for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+    for (int c = threadIdx.x; c < CL; c += blockDim.x) {
         int i, j, k;
         cell_of<D>(M, c, i, j, k);
         const int X = i >> 1, Y = j >> 1, Z = k >> 1;
-        const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
-        const T d0 = dc[pad_idx<D>(MC, X, Y, Z)], dx = dc[pad_idx<D>(MC, X + sx, Y, Z)];
-        const T dy = dc[pad_idx<D>(MC, X, Y + sy, Z)];
+        const int xs = X + ((i & 1) ? 1 : -1), ys = Y + ((j & 1) ? 1 : -1), zs = Z + ((k & 1) ? 1 : -1);
+        const T d0 = dc[pad_idx<D>(MC, X, Y, Z)];
+        const T dx = (xs >= 0 && xs < MC) ? dc[pad_idx<D>(MC, xs, Y, Z)] : -d0;
+        const T dy = (ys >= 0 && ys < MC) ? dc[pad_idx<D>(MC, X, ys, Z)] : -d0;
         const int q = pad_idx<D>(M, i, j, k);
-        if (D == 2) u[q] = fma(T(0.25), dx + dy, fma(T(0.5), d0, u[q]));
-        else u[q] = fma(T(0.25), ((d0 + dx) + dy) + dc[pad_idx<D>(MC, X, Y, Z + sz)], u[q]);
+        if (D == 2) {
+            u[q] = fma(T(0.25), dx + dy, fma(T(0.5), d0, u[q]));
+        } else {
+            const T dz = (zs >= 0 && zs < MC) ? dc[pad_idx<D>(MC, X, Y, zs)] : -d0;
+            u[q] = fma(T(0.25), ((d0 + dx) + dy) + dz, u[q]);
+        }
     }
     __syncthreads();
 }
 
+// dispatch on the box size of level index li (M = 2 << li)
+#define AFG_BT_M(li, CALL)                                  \
+    switch (li) {                                           \
+        case 0: { constexpr int MB = 2; CALL; break; }      \
+        case 1: { constexpr int MB = 4; CALL; break; }      \
+        case 2: { constexpr int MB = 8; CALL; break; }      \
+        default: { constexpr int MB = 16; CALL; break; }    \
+    }
+
 template <int D, typename T>
 __device__ void bt_vcycle(const BottomLevel *Ls, int lmin, int ltop, T *sm, T *dc, int nd, int nu, int nb, int hom) {
     for (int l = ltop; l > lmin; --l) {
-        bt_smooth<D, T>(Ls[l - lmin], sm, nd, hom);
-        bt_down<D, T>(Ls[l - lmin], Ls[l - 1 - lmin], sm, hom);
+        const int li = l - lmin;
+        AFG_BT_M(li, (bt_smooth<D, MB, T>(Ls[li], sm, nd, hom)));
+        AFG_BT_M(li, (bt_down<D, MB, T>(Ls[li], Ls[li - 1], sm, hom)));
     }
-    bt_smooth<D, T>(Ls[0], sm, nb, hom);
+    bt_smooth<D, 2, T>(Ls[0], sm, nb, hom);
     for (int l = lmin + 1; l <= ltop; ++l) {
-        bt_correct<D, T>(Ls[l - lmin], Ls[l - 1 - lmin], sm, dc);
-        bt_smooth<D, T>(Ls[l - lmin], sm, nu, hom);
+        const int li = l - lmin;
+        AFG_BT_M(li, (bt_correct<D, MB, T>(Ls[li], Ls[li - 1], sm, dc)));
+        AFG_BT_M(li, (bt_smooth<D, MB, T>(Ls[li], sm, nu, hom)));
     }
 }
 
@@ -238,7 +268,8 @@ __global__ void __launch_bounds__(kThreads) k_bottom(BoxMeta A, int ntrees, int 
             __syncthreads();
             if (l > lmin) {
                 // the FMG correction uses the copy stored at the start of step l-1
-                bt_correct<D, T>(L, Ls[l - 1 - lmin], sm, dc);
+                const int li = l - lmin;
+                AFG_BT_M(li, (bt_correct<D, MB, T>(L, Ls[li - 1], sm, dc)));
             }
             bt_vcycle<D, T>(Ls, lmin, l, sm, dc, nd, nu, nb, hom);
         }
