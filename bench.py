@@ -393,7 +393,11 @@ def main():
     lvl = max(range(1, info.highest_level + 1), key=lambda l: info.boxes_per_level[l])
     tree.set_rhs(rho)
     probe = tree.time_kernel(4, 0, True, 3)
-    fp64_peak_tflops = probe["flops"] / (probe["ms"] * 1e-3) / 1e12
+    probe_tflops = probe["flops"] / (probe["ms"] * 1e-3) / 1e12
+    # FP64 ALU peak from unit counts and clocks: SMs x max SM clock x 2 FP64 FMA per clock x 2 flops
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    fp64_peak_tflops = n_sm * sm_max * 1e6 * 2 * 2 / 1e12
     k64 = tree.time_kernel(0, lvl, True, 20)
     k32 = tree.time_kernel(0, lvl, False, 20)
     hbm = float(pk.get("hbm_gbs", 6800.0))
@@ -413,7 +417,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "k_smooth<3,8,double> (half-sweep, level %d)" % lvl,
                      "achieved": ach64, "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": ach64 / fp64_peak_tflops,
-                     "peak_source": "FP64 FMA probe run in this process (FMA = 2 flops)",
+                     "peak_source": "%d SMs x %.0f MHz x 2 FP64 FMA/clk x 2 flops (nominal 1.25 TFLOP/s)" % (n_sm, sm_max),
+                     "fp64_probe_tflops": probe_tflops, "frac_of_probe": ach64 / probe_tflops,
                      "ms": k64["ms"], "hbm_gbs": gbs64, "hbm_frac": gbs64 / hbm,
                      "traffic": TRAFFIC.get(("k_smooth<3,8,double>", lvl)), "traffic_unit": TRAFFIC_UNIT,
                      "algorithmic_bytes": k64["bytes"]},

@@ -761,7 +761,9 @@ int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, doub
     } else {
         nc = g.L(level).ncell;
         const double c2 = double(1 << D);
-        if (kernel == 0) { by = nc * 1.5 * sz; fl = nc * (2.0 * D + 2) / 2; }
+        // half-sweep, per update: 2D-1 additions and one FMA with the pre-scaled source (FP64),
+        // or 2D-1 additions, one FMA and one multiplication (FP32)
+        if (kernel == 0) { by = nc * 1.5 * sz; fl = nc * (2.0 * D + (w.rhoh_p() ? 1 : 2)) / 2; }
         if (kernel == 1) { by = nc * (2 * sz + 3 * sz / c2); fl = nc * (2.0 * D + 5); }
         if (kernel == 2) { by = nc * (2 * sz + 2 * sz / c2); fl = nc * 5.0; }
     }
