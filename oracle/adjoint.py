@@ -2,14 +2,15 @@
 
 Not in the paper (an addition): for a loss L(u) with u = A^-1(rho, b), the
 gradient is lam = K^-T dL/du (K = the composite leaf operator, Sec. 3.2-3.3)
-and dL/db_f = -(2/h^2) lam_i(f) (Dirichlet ghost 2b - u).  K is not symmetric
+and dL/db_f = -(2/h^2) lam_i(f) on Dirichlet sides (ghost 2b - u), -(1/h) lam_i(f)
+on Neumann sides (ghost u + h b).  K is not symmetric
 on refined trees (the conservative refinement-boundary ghosts couple fine to
 coarse with 1/2 but coarse to fine through the mean of the children), so the
 true transpose is needed.  Two solvers:
 
 * direct(): scipy sparse LU of K^T (the definition, for small trees);
 * bicgstab(): BiCGStab (van der Vorst 1992) with right preconditioner
-  W M W^-1, M = one oracle V-cycle from zero with homogeneous Dirichlet data,
+  W M W^-1, M = one oracle V-cycle from zero with homogeneous boundary data,
   W = diag(cell volumes) -- W K is symmetric up to the refinement-boundary
   terms, so W M W^-1 approximates K^-T.
 """
@@ -26,7 +27,8 @@ def direct(tree, g):
 
 def dl_db(tree, lam):
     e = tree.export()
-    _, B = composite.assemble(tree.D, tree.N, e["level"], e["idx"], e["children"])
+    _, B = composite.assemble(tree.D, tree.N, e["level"], e["idx"], e["children"],
+                              getattr(tree, "bc_types", None))
     return -(B.T @ lam)
 
 

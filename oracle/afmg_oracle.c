@@ -73,7 +73,8 @@ typedef struct {
     int nmg;
     OMG *mg;
     int mgstart[2 * OMAXLEV + 8], mgcount[2 * OMAXLEV + 8]; /* indexed by level - lmin */
-    int hom;                         /* 1: homogeneous Dirichlet data (defect equations) */
+    int hom;                         /* 1: homogeneous boundary data (defect equations) */
+    int bct[6];                      /* per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann */
 } OTree;
 
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
@@ -524,7 +525,8 @@ void ot_zero_solution(OTree *t) {
 /* Face cell f of side s: tangential coordinates (0-based) */
 static void face_tc(int M, int f, int *c1, int *c2) { *c1 = f % M; *c2 = f / M; }
 
-/* Dirichlet data on leaf boundary faces (canonical face order); coarse boxes
+/* Boundary data on leaf boundary faces (canonical face order): values on
+ * Dirichlet sides, outward normal derivatives on Neumann sides; coarse boxes
  * get the mean of the 2^(D-1) finer faces they cover.  Reading: the paper's
  * boundary routine is called per box; with data given only on leaf faces the
  * coarse values are their averages (they do not change the converged
@@ -576,9 +578,10 @@ static void side_cells(int M, int s, int *inner, int *second, int *ghost) {
 }
 
 /* Fill the side ghost cells of variable `which` (0 = u, 1 = d) of all boxes
- * of a level.  Same-level neighbour: copy.  Physical boundary (Dirichlet):
+ * of a level.  Same-level neighbour: copy.  Physical boundary, Dirichlet:
  * g = 2 b - u_1 (reading: b is the value at the face centre; the linear
- * extrapolation through it); for the correction d the data is homogeneous.
+ * extrapolation through it); Neumann: g = u_1 + h b (b the outward normal
+ * derivative); for the correction d the data is homogeneous.
  * Refinement boundary: the paper's default two-point conservative scheme,
  *   2D: g = u_H/2 + u_1 - (u_t + u_2)/4,
  *   3D: g = u_H/2 + 5/4 u_1 - (u_2 + u_t1 + u_t2)/4,
@@ -619,7 +622,8 @@ static void fill_ghosts(OTree *t, int level, int which) {
                     v[gi] = w[GI(M, pq[0], pq[1], pq[2])];
                 } else if (m->kind[s] == K_PHYS) {
                     double bval = (which == 0 && !t->hom) ? m->bc[s][f] : 0.0;
-                    v[gi] = 2.0 * bval - v[ii];
+                    if (t->bct[s] == 1) v[gi] = v[ii] + m->h * bval;
+                    else v[gi] = 2.0 * bval - v[ii];
                 } else if (which == 0) {
                     /* coarse-fine; only the solution u ever needs this */
                     OMG *q = &t->mg[m->nbid[s]];
@@ -888,6 +892,22 @@ void ot_apply_A(OTree *t, const double *u, double *out) {
 
 void ot_set_homogeneous(OTree *t, int hom) { t->hom = hom; }
 
+/* Boundary type of each domain side (Sec. 2 lists Dirichlet, Neumann and
+ * periodic conditions, given through ghost cells; Sec. 3 allows a mix).
+ * Reading: Neumann data b is the outward normal derivative at the face
+ * centre, and the ghost g = u_1 + h b makes the face flux (g - u_1)/h equal
+ * to b.  A tree with no Dirichlet side is singular and is refused. */
+int ot_set_bc_types(OTree *t, const int *types) {
+    int any_dirichlet = 0;
+    for (int s = 0; s < 2 * t->D; s++) {
+        if (types[s] != 0 && types[s] != 1) return -1;
+        any_dirichlet |= types[s] == 0;
+    }
+    if (!any_dirichlet) return -1;
+    for (int s = 0; s < 2 * t->D; s++) t->bct[s] = types[s];
+    return 0;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Composite operator as explicit rows: for leaf cell i the list of        */
 /* (leaf cell j, coefficient) with (A u)_i = sum_j K_ij u_j + boundary     */
@@ -923,7 +943,7 @@ long long ot_leaf_rows(OTree *t, int *row, int *col, double *val) {
                 memcpy(q, p, sizeof q);
                 q[a] += (s % 2) ? 1 : -1;
                 if (q[a] >= 1 && q[a] <= N) { PUT(me, leaf_cell_id(t, leafpos, mb, q[0], q[1], q[2]), ih2); continue; }
-                if (m->kind[s] == K_PHYS) { PUT(me, me, -ih2); continue; }
+                if (m->kind[s] == K_PHYS) { PUT(me, me, t->bct[s] == 1 ? ih2 : -ih2); continue; }
                 if (m->kind[s] == K_SAME) {
                     OMG *nbm = &t->mg[m->nbid[s]];
                     int qq[3]; memcpy(qq, q, sizeof qq);

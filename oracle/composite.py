@@ -9,7 +9,8 @@ faces the value across the face is found by dictionary lookups:
 * a refined cell of the same level: the mean of the 2^D fine cells under it
   (restriction by averaging, Sec. 2.5 -- at an FAS fixed point the coarse
   value equals the restriction of the fine values);
-* outside the domain: the Dirichlet ghost 2 b - u_i (b at the face centre);
+* outside the domain: the Dirichlet ghost 2 b - u_i (b the value at the face
+  centre), or the Neumann ghost u_i + h b (b the outward normal derivative);
 * a coarser leaf cell (refinement boundary): the default conservative
   two-point ghost of Sec. 3.3 (2D: u_H/2 + u_i - (u_t + u_n)/4; 3D:
   u_H/2 + 5/4 u_i - (u_n + u_t1 + u_t2)/4).
@@ -21,9 +22,11 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def assemble(dim, box_n, level, idx, children):
-    """level/idx/children: canonical box arrays (export format)."""
+def assemble(dim, box_n, level, idx, children, bc_types=None):
+    """level/idx/children: canonical box arrays (export format); bc_types: per
+    domain side (-x,+x,-y,+y[,-z,+z]) 0 = Dirichlet, 1 = Neumann (default all 0)."""
     D, N = dim, box_n
+    bct = list(bc_types) if bc_types is not None else [0] * (2 * D)
     nbox = len(level)
     is_leaf = children[:, 0] < 0
     leaf_ids = np.nonzero(is_leaf)[0]
@@ -67,11 +70,12 @@ def assemble(dim, box_n, level, idx, children):
                 q = g.copy()
                 q[a] += sgn
                 if q[a] < 0 or q[a] >= ncoarse:
-                    rows.append(me); cols.append(me); vals.append(-ih2)
+                    neumann = bct[s] == 1
+                    rows.append(me); cols.append(me); vals.append(ih2 if neumann else -ih2)
                     tang = [t for t in range(D) if t != a]
                     loc = offs[c]
                     f = loc[tang[0]] + (N * loc[tang[1]] if D == 3 else 0)
-                    brow.append(me); bcol.append(face_base[s] + f); bval.append(2.0 * ih2)
+                    brow.append(me); bcol.append(face_base[s] + f); bval.append(h * ih2 if neumann else 2.0 * ih2)
                     continue
                 key = (l,) + tuple(int(v) for v in q)
                 if key in leaf_cell:

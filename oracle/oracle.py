@@ -62,6 +62,7 @@ def lib():
             "ot_mg_set": (None, [P, I, I, P]), "ot_fill_ghosts": (None, [P, I, I]),
             "ot_smooth": (None, [P, I, I]), "ot_gsrb_half": (None, [P, I, I]),
             "ot_restrict": (None, [P, I, I]), "ot_correct": (None, [P, I]),
+            "ot_set_bc_types": (I, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -184,6 +185,14 @@ class OracleTree:
         u = np.zeros(self.n_leaf_cells)
         lib().ot_get_solution(self._h, _p(u))
         return u
+
+    def set_boundary_types(self, types):
+        """Per domain side (-x,+x,-y,+y[,-z,+z]): 0 Dirichlet, 1 Neumann."""
+        t = np.ascontiguousarray(types, dtype=np.int32)
+        assert t.size == 2 * self.D
+        if lib().ot_set_bc_types(self._h, _p(t)) != 0:
+            raise ValueError("boundary types must be 0/1 with at least one Dirichlet side")
+        self.bc_types = [int(v) for v in t]
 
     def set_homogeneous(self, hom):
         self._need_mg()
