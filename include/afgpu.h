@@ -134,12 +134,28 @@ int afg_info(const afg_tree *t, afg_tree_info *out);
 int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *parent,
                     int32_t *children, int32_t *neighbours);
 
+/* Boundary type of each domain side, types[2*dim] in the order -x,+x,-y,+y
+ * (,-z,+z): AFG_BC_DIRICHLET or AFG_BC_NEUMANN (Sec. 2 and Sec. 3 allow
+ * Dirichlet, Neumann or a mix, through ghost cells).  On a Neumann side the
+ * boundary datum (afg_set_dirichlet) is the outward normal derivative at the
+ * face centre and the ghost is u + h b; on a Dirichlet side it is the value
+ * and the ghost 2 b - u.  At least one side must be Dirichlet (a pure
+ * Neumann problem is singular): AFG_ERR_ARG otherwise, or for a value other
+ * than the two types, with the tree unchanged.  Host call; like a tree
+ * change it discards the device fields, so set rho and the boundary data
+ * after it.  Default: all sides Dirichlet.  Trees of a forest keep the types
+ * they had when the forest was created. */
+#define AFG_BC_DIRICHLET 0
+#define AFG_BC_NEUMANN 1
+int afg_set_boundary_types(afg_tree *t, const int *types_host);
+
 /* ---- fields (device memory, enqueued on the tree's stream) ------------- */
 
 /* Source term rho on leaf cells (n_leaf_cells doubles). */
 int afg_set_rhs(afg_tree *t, const double *rho_leaf_dev);
-/* Dirichlet values at the leaf boundary face centres (n_bfaces doubles);
- * the ghost value is 2 b - u (Sec. 2.4).  Coarse boxes use face averages.
+/* Boundary data at the leaf boundary face centres (n_bfaces doubles):
+ * Dirichlet values (ghost 2 b - u, Sec. 2.4) or, on Neumann sides, outward
+ * normal derivatives (ghost u + h b).  Coarse boxes use face averages.
  * Without this call the boundary data is zero. */
 int afg_set_dirichlet(afg_tree *t, const double *b_face_dev);
 /* Initial guess / warm start on leaf cells; without it the guess is zero. */
@@ -161,8 +177,9 @@ int afg_residual_norm(afg_tree *t, double *max_abs_r, double *max_abs_rho);
 
 /* Adjoint of the solve: given g = dL/du on leaf cells, solve K^T lambda = g
  * for the transposed composite operator (FP64) and return lambda = dL/drho
- * (leaf cells) and dL/db = -(2/h^2) lambda at the boundary-adjacent cell of
- * every leaf boundary face.  Output pointers may be NULL. */
+ * (leaf cells) and dL/db = -(2/h^2) lambda (Dirichlet side) or -(1/h) lambda
+ * (Neumann side) at the boundary-adjacent cell of every leaf boundary face.
+ * Output pointers may be NULL. */
 int afg_adjoint(afg_tree *t, const double *g_leaf_dev, double *lambda_leaf_dev,
                 double *dL_db_face_dev, const afg_mg_opts *opts, afg_stats *stats);
 

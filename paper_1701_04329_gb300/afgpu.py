@@ -16,6 +16,7 @@ from . import build as _build
 
 AFG_OK, AFG_ERR_ARG, AFG_ERR_CUDA, AFG_ERR_NOMEM, AFG_ERR_STATE, AFG_ERR_NOT_CONVERGED, AFG_ERR_TIMEOUT = (
     0, -1, -2, -3, -4, -5, -6)
+AFG_BC_DIRICHLET, AFG_BC_NEUMANN = 0, 1
 AFG_FP64, AFG_MIXED = 0, 1
 
 
@@ -56,6 +57,7 @@ _SIGS = {
     "afg_refine_uniform": (I, [P, I]), "afg_cell_centers": (I, [P, P]), "afg_face_centers": (I, [P, P]),
     "afg_leaf_levels": (I, [P, P]), "afg_adapt": (I, [P, P, I, P, P]), "afg_info": (I, [P, P]),
     "afg_export_tree": (I, [P, P, P, P, P, P]), "afg_set_rhs": (I, [P, P]), "afg_set_dirichlet": (I, [P, P]),
+    "afg_set_boundary_types": (I, [P, P]),
     "afg_set_solution": (I, [P, P]), "afg_get_solution": (I, [P, P]), "afg_fmg": (I, [P, P, P]),
     "afg_vcycle": (I, [P, P, P]), "afg_solve": (I, [P, P, P]), "afg_residual_norm": (I, [P, P, P]),
     "afg_adjoint": (I, [P, P, P, P, P, P]), "afg_forest_create": (I, [I, P, P]), "afg_forest_destroy": (I, [P]),
@@ -214,6 +216,14 @@ class Tree:
     def set_dirichlet(self, b):
         self._sync_stream()
         _check(lib().afg_set_dirichlet(self._h, _dev(b, self.n_bfaces)))
+
+    def set_boundary_types(self, types):
+        """Per domain side (-x,+x,-y,+y[,-z,+z]): AFG_BC_DIRICHLET or
+        AFG_BC_NEUMANN.  Discards the device fields: set rho and b after it."""
+        t = np.ascontiguousarray(types, dtype=np.int32)
+        if t.size != 2 * self.D:
+            raise ValueError("need %d boundary types" % (2 * self.D))
+        _check(lib().afg_set_boundary_types(self._h, t.ctypes.data_as(P)))
 
     def set_solution(self, u):
         self._sync_stream()

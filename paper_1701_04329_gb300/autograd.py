@@ -3,7 +3,8 @@
 Forward: the FAS multigrid solve of the library (arXiv:1701.04329 Sec. 3).
 Backward (an addition to the paper): the library's adjoint solve
 K^T lam = dL/du for the transposed composite operator; dL/drho = lam and
-dL/db = -(2/h^2) lam at the cell next to each boundary face.
+dL/db = -(2/h^2) lam (Dirichlet side) or -(1/h) lam (Neumann side) at the
+cell next to each boundary face.
 """
 import torch
 

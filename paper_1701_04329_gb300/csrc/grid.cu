@@ -159,8 +159,15 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
         }
     n_leaf_cells = (long long)n_leaf_boxes * (D == 2 ? N * N : N * N * N);
 
+    // Neumann domain sides of every box (bit s), from its tree's side types
+    std::vector<unsigned char> nmask(nbox, 0);
+    for (int g = 0; g < nbox; ++g)
+        for (int s = 0; s < S; ++s)
+            if (nb[g * S + s] == -1 && trees[tree[g]]->bct[s] == 1) nmask[g] |= (unsigned char)(1u << s);
+
     auto &own = owned;
     meta.nb = upload(nb, own);
+    meta.nmask = upload(nmask, own);
     meta.parent = upload(parent, own);
     meta.poff = upload(poff, own);
     meta.coff = upload(coff, own);

@@ -34,6 +34,7 @@ class HostTree {
     std::vector<long long> leaf_face0; // first canonical boundary face of leaf i
     long long n_leaf_cells = 0, n_bfaces = 0;
     int version = 0;                   // bumped on every change
+    int bct[6] = {0, 0, 0, 0, 0, 0};   // per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann
 
     int ndir() const;                  // 3^D - 1
     int side_dir(int s) const;         // face side (-x,+x,-y,...) -> direction index

@@ -56,6 +56,7 @@ struct BoxMeta {
     const double *hb;   // cell size of every box
     const long long *nbase;  // per side: cells of the neighbour / coarse box, or Dirichlet data offset
     const double *ih2;       // 1/h^2 of every box (an FP64 division costs ~11 FP64-pipe instructions)
+    const unsigned char *nmask;  // bit s: side s is a Neumann domain boundary (ghost u + h b, not 2 b - u)
 };
 
 // Metadata of one box, prefetched into shared memory one box ahead.
@@ -65,6 +66,8 @@ struct BoxInfo {
     int code[6];
     int b, flag, poff, parent;
     long long pcoff;  // cells of the parent (k_correct)
+    int nmask;        // Neumann domain sides (of the parent in k_correct)
+    double h;         // cell size
 };
 
 // The activity mask is written by kernels: after pdl_wait, drop a prefetched
@@ -97,6 +100,8 @@ __device__ __forceinline__ void info_load(const BoxMeta &A, int idx, int n, int 
                 I.flag = A.bflag[b];
                 I.poff = A.poff[b];
                 I.parent = A.parent[b];
+                I.nmask = A.nmask[b];
+                I.h = A.hb[b];
             }
         }
     }
@@ -312,8 +317,8 @@ __device__ __forceinline__ void finalize(const BoxInfo &I, T *tile, int lt, int 
         const int gidx = ti<D, M>(i, j, k);
         face_pos(D, s, pin, t1, t2, i, j, k);
         const T u1 = tile[ti<D, M>(i, j, k)];
-        if (code == -1) {
-            tile[gidx] = T(2) * tile[gidx] - u1;
+        if (code == -1) {  // the slot holds b: Dirichlet 2b - u_1, Neumann u_1 + h b
+            tile[gidx] = ((I.nmask >> s) & 1) ? fma(T(I.h), tile[gidx], u1) : T(2) * tile[gidx] - u1;
         } else {
             const T uH = tile[gidx];
             face_pos(D, s, p2, t1, t2, i, j, k);
@@ -665,6 +670,7 @@ __device__ __forceinline__ void pinfo_load(const BoxMeta &A, int idx, int n, int
                 I.poff = A.poff[b];
                 I.parent = A.parent[b];
                 I.pcoff = A.coff[I.parent];
+                I.nmask = A.nmask[I.parent];
             }
         }
     }
@@ -739,10 +745,10 @@ __global__ void __launch_bounds__(kThreads) k_correct(BoxMeta A, int b0, int n, 
                         pc[a] = (side & 1) ? 0 : MP - 1;
                         const long long q = I.base[side] + rbi<D, MP>(pc[0], pc[1], pc[2]);
                         d = u[q] - vold[q];
-                    } else {
+                    } else {  // domain boundary: homogeneous ghost of the difference, -d (Dirichlet) or d (Neumann)
                         pc[a] = (side & 1) ? MP - 1 : 0;
                         const long long q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
-                        d = -(u[q] - vold[q]);
+                        d = ((I.nmask >> side) & 1) ? u[q] - vold[q] : -(u[q] - vold[q]);
                     }
                 }
                 dt[di(x, y, z)] = d;

@@ -135,7 +135,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
             const T u1 = gv;
             if (code == -1) {
                 const T bv = hom ? T(0) : T(A.bc[I.base[s] + k * M + j]);
-                gv = T(2) * bv - u1;
+                gv = ((I.nmask >> s) & 1) ? fma(T(I.h), bv, u1) : T(2) * bv - u1;
             } else {
                 const int iin = s ? M - 1 : 0, p2 = s ? M - 2 : 1;
                 const int cj = unpack_off(I.poff, 1) + (j >> 1);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
                 if (code == -1) {
                     const int t2 = a == 1 ? kin : jin;
                     const T bv = hom ? T(0) : T(A.bc[I.base[s] + t2 * M + i]);
-                    gv[x] = T(2) * bv - u1;
+                    gv[x] = ((I.nmask >> s) & 1) ? fma(T(I.h), bv, u1) : T(2) * bv - u1;
                 } else {
                     const int ci = unpack_off(I.poff, 0) + (i >> 1);
                     int cj, ck;
@@ -456,7 +456,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual_p(BoxMeta A, const i
 // version of k_correct: a box's own values (16-byte copies) and the parent's
 // v_H and v'_H over the box's parent region plus one layer (scalar copies;
 // outside the parent from its same-level neighbour, or mirrored inside it at
-// the domain boundary, where the difference changes sign) arrive by cp.async
+// the domain boundary, where the difference changes sign on Dirichlet sides
+// and keeps it on Neumann sides) arrive by cp.async
 // one box ahead; d = v_H - v'_H is formed once per staged value, then the
 // 2-1-1 / 1-1-1-1 prolongation (Sec. 2.5) is added.
 // ---------------------------------------------------------------------------
@@ -520,7 +521,8 @@ __device__ __forceinline__ void cp_issue(const BoxInfo &I, const T *u, const T *
             if (I.code[side] >= 0) {
                 pc[a] = (side & 1) ? 0 : MP - 1;
                 q = I.base[side] + rbi<D, MP>(pc[0], pc[1], pc[2]);
-            } else {  // domain boundary: the mirrored cell (a refined box has no coarser neighbour)
+            } else {  // domain boundary: the mirrored cell (a refined box has no coarser neighbour);
+                      // its difference enters as -d (Dirichlet) or d (Neumann)
                 pc[a] = (side & 1) ? MP - 1 : 0;
                 q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
             }
@@ -563,13 +565,14 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
         pinfo_load<D>(A, base + NST * stride + g, n, b0, info[((it + NST) % NI) * S::BPC + g], lt, S::G, true);
         T *U = st, *DU = st + S::C;
         const T *DV = DU + S::QCP;
-        if (I.b >= 0) {  // d = v_H - v'_H in place, negated across the domain boundary
+        if (I.b >= 0) {  // d = v_H - v'_H in place, negated across a Dirichlet domain boundary
             for (int c = lt; c < S::QC; c += S::G) {
                 int x, y, z;
                 if (!cp_slot<D, M>(c, x, y, z)) continue;
                 int pc[3];
                 const int side = cp_side<D, M, MP>(I, x, y, z, pc);
-                DU[c] = (side >= 0 && I.code[side] < 0) ? DV[c] - DU[c] : DU[c] - DV[c];
+                const bool flip = side >= 0 && I.code[side] < 0 && !((I.nmask >> side) & 1);
+                DU[c] = flip ? DV[c] - DU[c] : DU[c] - DV[c];
             }
         }
         __syncthreads();

@@ -94,8 +94,8 @@ __global__ void __launch_bounds__(kThreads) k_mixed_update(BoxMeta A, const int 
 // ghost (coarse value 1/2, own cell 1 (2D) or 5/4 (3D), next inward and
 // tangential partner(s) -1/4).  Its transpose is gathered per cell:
 //   * ghost slots carry the symmetric part: same-level leaf lam; 2 * sum of
-//     the 2^(D-1) adjacent fine lam for a refined neighbour; -lam (Dirichlet);
-//     c1 * lam (refinement boundary);
+//     the 2^(D-1) adjacent fine lam for a refined neighbour; -lam (Dirichlet),
+//     +lam (Neumann); c1 * lam (refinement boundary);
 //   * at a refinement-boundary side the two cell layers next to it add
 //     lam_C / 2^(D+2) (the coarse leaf's equation averages them), the first
 //     layer adds -1/4 lam of its tangential partner(s), the second layer
@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_apply(BoxMeta A, const int
                                 sum += lam[A.coff[cbx] + rbi<D, M>(fc[0] % M, fc[1] % M, D == 3 ? fc[2] % M : 0)];
                             }
                         v = 2.0 * sum;
-                    } else if (code == -1) {
-                        v = -self;
+                    } else if (code == -1) {  // the ghost's own-cell weight: -1 (2b - u) or +1 (u + h b)
+                        v = ((A.nmask[b] >> s) & 1) ? self : -self;
                     } else {
                         v = c1 * self;
                     }
@@ -224,7 +224,9 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_db(BoxMeta A, const double
                 const int t1 = f % M, t2 = D == 3 ? f / M : 0;
                 int i, j, k;
                 face_pos(D, s, pin, t1, t2, i, j, k);
-                db[A.bcoff[b * 2 * D + s] + f] = -2.0 / (h * h) * lam[A.coff[b] + rbi<D, M>(i, j, k)];
+                // dA/db: 2/h^2 (Dirichlet ghost 2b - u) or 1/h (Neumann ghost u + h b)
+                const double w = ((A.nmask[b] >> s) & 1) ? 1.0 / h : 2.0 / (h * h);
+                db[A.bcoff[b * 2 * D + s] + f] = -w * lam[A.coff[b] + rbi<D, M>(i, j, k)];
             }
         }
     }

@@ -49,3 +49,24 @@ def test_errors_are_status_codes():
     except afgpu.AfgError as e:
         assert e.code == afgpu.AFG_ERR_ARG
     assert t.info().n_boxes == 1  # failed calls left the tree unchanged
+
+
+def test_boundary_types_validated_on_the_host():
+    """afg_set_boundary_types: 0/1 per side, at least one Dirichlet side;
+    a refused call leaves the types (and the tree) unchanged."""
+    import numpy as np
+    t = afgpu.Tree(2, 8, 4)
+    t.refine_uniform(2)
+    for bad in ([1, 1, 1, 1], [0, 2, 0, 0], [0, -1, 0, 0]):
+        try:
+            t.set_boundary_types(bad)
+            assert False, bad
+        except afgpu.AfgError as e:
+            assert e.code == afgpu.AFG_ERR_ARG
+    t.set_boundary_types([afgpu.AFG_BC_NEUMANN, afgpu.AFG_BC_DIRICHLET, afgpu.AFG_BC_NEUMANN, afgpu.AFG_BC_DIRICHLET])
+    assert t.info().n_boxes == 5
+    try:
+        t.set_boundary_types([1, 0, 1])  # wrong count for 2D
+        assert False
+    except ValueError:
+        pass
