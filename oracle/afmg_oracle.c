@@ -74,8 +74,16 @@ typedef struct {
     OMG *mg;
     int mgstart[2 * OMAXLEV + 8], mgcount[2 * OMAXLEV + 8]; /* indexed by level - lmin */
     int hom;                         /* 1: homogeneous boundary data (defect equations) */
-    int bct[6];                      /* per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann */
+    int bct[6];                      /* per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann, 2 periodic */
 } OTree;
+
+/* spatial index q along axis a at a level with `side` boxes per axis: on a
+ * periodic axis it wraps around (Sec. 2.2: the box beyond the last one is
+ * the first), elsewhere it is returned as is */
+static int pwrap(const OTree *t, int a, int q, int side) {
+    if (t->bct[2 * a] != 2) return q;
+    return ((q - 1) % side + side) % side + 1;
+}
 
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
 
@@ -167,7 +175,7 @@ static int rebuild(OTree *t, OPos *pos, int n) {
             int off[3], q[3] = {1, 1, 1}, outside = 0;
             dir_offsets(t->D, d, off);
             for (int a = 0; a < t->D; a++) {
-                q[a] = b->idx[a] + off[a];
+                q[a] = pwrap(t, a, b->idx[a] + off[a], side);
                 if (q[a] < 1 || q[a] > side) outside = 1;
             }
             b->nb[d] = outside ? -2 : find_box(t, b->level, q);
@@ -347,7 +355,7 @@ int ot_adapt(OTree *t, const signed char *flags, int nbuf, int *n_added, int *n_
                 if (t->box[b].nb[d] != -1) continue;
                 int off[3], q[3] = {1, 1, 1};
                 dir_offsets(D, d, off);
-                for (int a = 0; a < D; a++) q[a] = (t->box[b].idx[a] + off[a] + 1) / 2;
+                for (int a = 0; a < D; a++) q[a] = (pwrap(t, a, t->box[b].idx[a] + off[a], 1 << (l - 1)) + 1) / 2;
                 int c = find_box(t, l - 1, q);
                 if (c < 0 || !isleaf[c]) { free(ref); free(rm); free(isleaf); free(leafpos); return -4; }
                 ref[c] = 1;
@@ -439,7 +447,11 @@ int ot_mg_setup(OTree *t) {
         m->tbox = -1;
         m->parent = i > 0 ? i - 1 : -1;
         m->refined = 1;
-        for (int s = 0; s < 2 * D; s++) { m->kind[s] = K_PHYS; m->nbid[s] = -1; }
+        for (int s = 0; s < 2 * D; s++) {
+            /* one box per level: across a periodic side it is its own neighbour */
+            if (t->bct[s] == 2) { m->kind[s] = K_SAME; m->nbid[s] = i; }
+            else { m->kind[s] = K_PHYS; m->nbid[s] = -1; }
+        }
         t->mgstart[m->level - t->lmin] = i; t->mgcount[m->level - t->lmin] = 1;
     }
     for (int b = 0; b < t->nbox; b++) {
@@ -896,15 +908,26 @@ void ot_set_homogeneous(OTree *t, int hom) { t->hom = hom; }
  * periodic conditions, given through ghost cells; Sec. 3 allows a mix).
  * Reading: Neumann data b is the outward normal derivative at the face
  * centre, and the ghost g = u_1 + h b makes the face flux (g - u_1)/h equal
- * to b.  A tree with no Dirichlet side is singular and is refused. */
+ * to b.  Periodic (Sec. 2.2: the neighbour beyond the last box is the first)
+ * applies to both sides of an axis; it changes the connectivity, so it can
+ * only be switched on or off while the tree is the root box alone.  A tree
+ * with no Dirichlet side is singular and is refused. */
 int ot_set_bc_types(OTree *t, const int *types) {
-    int any_dirichlet = 0;
+    int any_dirichlet = 0, change = 0;
     for (int s = 0; s < 2 * t->D; s++) {
-        if (types[s] != 0 && types[s] != 1) return -1;
+        if (types[s] < 0 || types[s] > 2) return -1;
+        if ((types[s] == 2) != (types[s ^ 1] == 2)) return -1;
         any_dirichlet |= types[s] == 0;
+        change |= (types[s] == 2) != (t->bct[s] == 2);
     }
     if (!any_dirichlet) return -1;
+    if (change && t->nbox != 1) return -1;
     for (int s = 0; s < 2 * t->D; s++) t->bct[s] = types[s];
+    if (change) {
+        OPos root = {1, 0, {1, 1, 1}};
+        root.key = morton_key(t->D, root.idx);
+        return rebuild(t, &root, 1);
+    }
     return 0;
 }
 

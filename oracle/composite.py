@@ -11,6 +11,7 @@ faces the value across the face is found by dictionary lookups:
   value equals the restriction of the fine values);
 * outside the domain: the Dirichlet ghost 2 b - u_i (b the value at the face
   centre), or the Neumann ghost u_i + h b (b the outward normal derivative);
+  across a periodic side the lookup wraps around to the opposite side;
 * a coarser leaf cell (refinement boundary): the default conservative
   two-point ghost of Sec. 3.3 (2D: u_H/2 + u_i - (u_t + u_n)/4; 3D:
   u_H/2 + 5/4 u_i - (u_n + u_t1 + u_t2)/4).
@@ -24,9 +25,11 @@ import scipy.sparse as sp
 
 def assemble(dim, box_n, level, idx, children, bc_types=None):
     """level/idx/children: canonical box arrays (export format); bc_types: per
-    domain side (-x,+x,-y,+y[,-z,+z]) 0 = Dirichlet, 1 = Neumann (default all 0)."""
+    domain side (-x,+x,-y,+y[,-z,+z]) 0 = Dirichlet, 1 = Neumann, 2 = periodic
+    (default all 0)."""
     D, N = dim, box_n
     bct = list(bc_types) if bc_types is not None else [0] * (2 * D)
+    periodic = [bct[2 * a] == 2 for a in range(D)]
     nbox = len(level)
     is_leaf = children[:, 0] < 0
     leaf_ids = np.nonzero(is_leaf)[0]
@@ -57,6 +60,8 @@ def assemble(dim, box_n, level, idx, children, bc_types=None):
         face_base = {}
         for s in range(2 * D):
             a, hi = s // 2, s % 2
+            if periodic[a]:
+                continue
             if (hi == 0 and idx[b][a] == 1) or (hi == 1 and idx[b][a] == 2 ** (l - 1)):
                 face_base[s] = nface
                 nface += N ** (D - 1)
@@ -69,6 +74,8 @@ def assemble(dim, box_n, level, idx, children, bc_types=None):
                 a, sgn = s // 2, (1 if s % 2 else -1)
                 q = g.copy()
                 q[a] += sgn
+                if periodic[a]:
+                    q[a] %= ncoarse
                 if q[a] < 0 or q[a] >= ncoarse:
                     neumann = bct[s] == 1
                     rows.append(me); cols.append(me); vals.append(ih2 if neumann else -ih2)
@@ -110,14 +117,17 @@ def cell_volumes(dim, box_n, level, children):
     return np.repeat(h ** dim, box_n ** dim)
 
 
-def face_areas(dim, box_n, level, idx, children):
+def face_areas(dim, box_n, level, idx, children, bc_types=None):
     """h^(D-1) for each boundary face, canonical face order."""
+    bct = list(bc_types) if bc_types is not None else [0] * (2 * dim)
     out = []
     for b in np.nonzero(children[:, 0] < 0)[0]:
         l = int(level[b])
         h = 1.0 / (box_n * 2 ** (l - 1))
         for s in range(2 * dim):
             a, hi = s // 2, s % 2
+            if bct[2 * a] == 2:
+                continue
             if (hi == 0 and idx[b][a] == 1) or (hi == 1 and idx[b][a] == 2 ** (l - 1)):
                 out.extend([h ** (dim - 1)] * box_n ** (dim - 1))
     return np.array(out)

@@ -187,11 +187,13 @@ class OracleTree:
         return u
 
     def set_boundary_types(self, types):
-        """Per domain side (-x,+x,-y,+y[,-z,+z]): 0 Dirichlet, 1 Neumann."""
+        """Per domain side (-x,+x,-y,+y[,-z,+z]): 0 Dirichlet, 1 Neumann, 2 periodic
+        (both sides of an axis; switched only while the tree is the root box)."""
         t = np.ascontiguousarray(types, dtype=np.int32)
         assert t.size == 2 * self.D
         if lib().ot_set_bc_types(self._h, _p(t)) != 0:
-            raise ValueError("boundary types must be 0/1 with at least one Dirichlet side")
+            raise ValueError("boundary types: 0/1/2, periodic in pairs and set on the root box alone, "
+                             "at least one Dirichlet side")
         self.bc_types = [int(v) for v in t]
 
     def set_homogeneous(self, hom):

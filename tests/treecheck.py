@@ -23,7 +23,8 @@ def directions(D):
     return out
 
 
-def check_tree(e, D, N=None):
+def check_tree(e, D, N=None, periodic=()):
+    """periodic: axes whose neighbours wrap around (Sec. 2.2)."""
     level, idx, parent, children, nbs = e["level"], e["idx"], e["parent"], e["children"], e["neighbours"]
     n = len(level)
     pos = {(int(level[b]),) + tuple(int(v) for v in idx[b]): b for b in range(n)}
@@ -45,6 +46,7 @@ def check_tree(e, D, N=None):
         assert all(k >= 0 for k in kids) or all(k < 0 for k in kids)  # never partially refined
         for d, off in enumerate(dirs):
             q = [int(idx[b][a]) + off[a] for a in range(D)]
+            q = [(v - 1) % side + 1 if a in periodic else v for a, v in enumerate(q)]
             if any(v < 1 or v > side for v in q):
                 assert nbs[b, d] == -2
             else:
@@ -58,8 +60,11 @@ def check_tree(e, D, N=None):
     lo = np.array([(idx[b] - 1) / 2.0 ** (level[b] - 1) for b in leaves])
     hi = lo + np.array([1.0 / 2.0 ** (level[b] - 1) for b in leaves])[:, None]
     lv = level[leaves]
+    shifts = [s for s in itertools.product((-1, 0, 1), repeat=D) if all(s[a] == 0 or a in periodic for a in range(D))]
     for i in range(len(leaves)):
-        touch = np.all((lo <= hi[i] + 1e-12) & (hi >= lo[i] - 1e-12), axis=1)
-        assert np.all(np.abs(lv[touch] - lv[i]) <= 1), "2:1 balance violated"
+        for sh in shifts:  # periodic images touch across the wrapped sides
+            lo_i, hi_i = lo[i] + np.array(sh), hi[i] + np.array(sh)
+            touch = np.all((lo <= hi_i + 1e-12) & (hi >= lo_i - 1e-12), axis=1)
+            assert np.all(np.abs(lv[touch] - lv[i]) <= 1), "2:1 balance violated"
     # leaves tile the domain
     assert abs(sum(1.0 / 2.0 ** (D * (level[b] - 1)) for b in leaves) - 1.0) < 1e-12
