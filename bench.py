@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--uniform-level", type=int, default=6)
     ap.add_argument("--inner", type=int, default=None, help="FP32 V-cycles per FP64 residual (mixed solves)")
+    ap.add_argument("--bc", default=None,
+                    help="--solve-only: side types -x,+x,-y,+y[,-z,+z] as letters D (Dirichlet) / N (Neumann, "
+                         "zero outward derivative) / P (periodic, in pairs), e.g. NNDDDD or PPDDPP")
     ap.add_argument("--workload", default="twosrc3d", choices=["twosrc3d", "gauss2d", "blobs3d"],
                     help="problem of the --solve-only mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -108,8 +111,16 @@ def solve_only(args):
     p = {"twosrc3d": lambda: W.twosrc3d(uniform_level=args.uniform_level), "gauss2d": W.gauss2d,
          "blobs3d": W.blobs3d}[args.workload]()
     t = afgpu.Tree(p.dim, p.box_n, p.max_level)
+    if args.bc:  # before the tree is built: periodicity is part of the connectivity
+        code = {"D": afgpu.AFG_BC_DIRICHLET, "N": afgpu.AFG_BC_NEUMANN, "P": afgpu.AFG_BC_PERIODIC}
+        t.set_boundary_types([code[c] for c in args.bc.upper()])
     p.build(t)
     rho_h, b_h = p.data(t)
+    if args.bc:  # zero outward derivative on the Neumann sides, the workload's values elsewhere
+        xf = t.face_centers()
+        for s, c in enumerate(args.bc.upper()):
+            if c == "N":
+                b_h[xf[:, s // 2] == float(s % 2)] = 0.0
     rho, bv = torch.tensor(rho_h, device="cuda"), torch.tensor(b_h, device="cuda")
     zero = torch.zeros_like(rho)
     prec = afgpu.AFG_MIXED if args.solve_only == "mixed" else afgpu.AFG_FP64
@@ -127,7 +138,8 @@ def solve_only(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             ms.append((time.perf_counter() - t0) * 1e3)
-    print(json.dumps({"solve": args.solve_only, "workload": args.workload, "unknowns": t.n_leaf_cells, "ms": ms,
+    print(json.dumps({"solve": args.solve_only, "workload": args.workload, "bc": args.bc or "all Dirichlet",
+                      "unknowns": t.n_leaf_cells, "ms": ms,
                       "cycles": st["cycles"], "rel": st["rel_residual"]}))
 
 

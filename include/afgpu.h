@@ -135,18 +135,22 @@ int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *pa
                     int32_t *children, int32_t *neighbours);
 
 /* Boundary type of each domain side, types[2*dim] in the order -x,+x,-y,+y
- * (,-z,+z): AFG_BC_DIRICHLET or AFG_BC_NEUMANN (Sec. 2 and Sec. 3 allow
- * Dirichlet, Neumann or a mix, through ghost cells).  On a Neumann side the
- * boundary datum (afg_set_dirichlet) is the outward normal derivative at the
- * face centre and the ghost is u + h b; on a Dirichlet side it is the value
- * and the ghost 2 b - u.  At least one side must be Dirichlet (a pure
- * Neumann problem is singular): AFG_ERR_ARG otherwise, or for a value other
- * than the two types, with the tree unchanged.  Host call; like a tree
- * change it discards the device fields, so set rho and the boundary data
- * after it.  Default: all sides Dirichlet.  Trees of a forest keep the types
- * they had when the forest was created. */
+ * (,-z,+z): AFG_BC_DIRICHLET, AFG_BC_NEUMANN or AFG_BC_PERIODIC (Sec. 2 and
+ * Sec. 3 allow Dirichlet, Neumann, periodic or a mix, through ghost cells).
+ * On a Neumann side the boundary datum (afg_set_dirichlet) is the outward
+ * normal derivative at the face centre and the ghost is u + h b; on a
+ * Dirichlet side it is the value and the ghost 2 b - u.  Periodic applies to
+ * both sides of an axis and is a property of the connectivity (Sec. 2.2: the
+ * box beyond the last one is the first): those sides carry no boundary faces,
+ * and periodicity can only be switched while the tree is the root box alone
+ * (set it before refining).  At least one side must be Dirichlet (the problem
+ * is singular otherwise).  AFG_ERR_ARG for any violation, with the tree
+ * unchanged.  Host call; a change discards the device fields, so set rho and
+ * the boundary data after it.  Default: all sides Dirichlet.  Trees of a
+ * forest keep the types they had when the forest was created. */
 #define AFG_BC_DIRICHLET 0
 #define AFG_BC_NEUMANN 1
+#define AFG_BC_PERIODIC 2
 int afg_set_boundary_types(afg_tree *t, const int *types_host);
 
 /* ---- fields (device memory, enqueued on the tree's stream) ------------- */

@@ -16,7 +16,7 @@ from . import build as _build
 
 AFG_OK, AFG_ERR_ARG, AFG_ERR_CUDA, AFG_ERR_NOMEM, AFG_ERR_STATE, AFG_ERR_NOT_CONVERGED, AFG_ERR_TIMEOUT = (
     0, -1, -2, -3, -4, -5, -6)
-AFG_BC_DIRICHLET, AFG_BC_NEUMANN = 0, 1
+AFG_BC_DIRICHLET, AFG_BC_NEUMANN, AFG_BC_PERIODIC = 0, 1, 2
 AFG_FP64, AFG_MIXED = 0, 1
 
 
@@ -218,8 +218,9 @@ class Tree:
         _check(lib().afg_set_dirichlet(self._h, _dev(b, self.n_bfaces)))
 
     def set_boundary_types(self, types):
-        """Per domain side (-x,+x,-y,+y[,-z,+z]): AFG_BC_DIRICHLET or
-        AFG_BC_NEUMANN.  Discards the device fields: set rho and b after it."""
+        """Per domain side (-x,+x,-y,+y[,-z,+z]): AFG_BC_DIRICHLET,
+        AFG_BC_NEUMANN or AFG_BC_PERIODIC (pairs; set on the root box before
+        refining).  Discards the device fields: set rho and b after it."""
         t = np.ascontiguousarray(types, dtype=np.int32)
         if t.size != 2 * self.D:
             raise ValueError("need %d boundary types" % (2 * self.D))

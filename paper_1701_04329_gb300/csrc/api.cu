@@ -441,18 +441,11 @@ int afg_adapt(afg_tree *t, const int8_t *flags, int n_buf, int *n_added, int *n_
 
 int afg_set_boundary_types(afg_tree *t, const int *types) {
     if (!t || !types) return fail(AFG_ERR_ARG, "null argument");
-    bool any_dirichlet = false;
-    for (int s = 0; s < 2 * t->ht.D; ++s) {
-        if (types[s] != AFG_BC_DIRICHLET && types[s] != AFG_BC_NEUMANN) return fail(AFG_ERR_ARG, "unknown boundary type");
-        any_dirichlet |= types[s] == AFG_BC_DIRICHLET;
-    }
-    if (!any_dirichlet) return fail(AFG_ERR_ARG, "at least one side must be Dirichlet (a pure Neumann problem is singular)");
-    bool same = true;
-    for (int s = 0; s < 2 * t->ht.D; ++s) same &= t->ht.bct[s] == types[s];
-    if (same) return AFG_OK;
-    for (int s = 0; s < 2 * t->ht.D; ++s) t->ht.bct[s] = types[s];
-    ++t->ht.version;  // the device grid is rebuilt (boundary metadata changes)
+    AFG_API_BEGIN
+    std::string err;  // a change rebuilds the host tree (new version: the device grid follows)
+    if (t->ht.set_boundary_types(types, err)) return fail(AFG_ERR_ARG, err);
     return AFG_OK;
+    AFG_API_END
 }
 
 int afg_info(const afg_tree *t, afg_tree_info *out) {

@@ -98,6 +98,8 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
             bflag[g] = BF_REFINED | BF_SPECIAL;
             tree[g] = t;
             child[g * NC] = i + 1 < nsub ? sub[t][i + 1] : gid[t][0];
+            for (int s = 0; s < S; ++s)  // one box per level: its own neighbour across a periodic side
+                if (ht.bct[s] == 2) nb[g * S + s] = g;
         }
         for (int b = 0; b < (int)ht.boxes.size(); ++b) {
             const HBox &hx = ht.boxes[b];
@@ -161,9 +163,11 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
 
     // Neumann domain sides of every box (bit s), from its tree's side types
     std::vector<unsigned char> nmask(nbox, 0);
-    for (int g = 0; g < nbox; ++g)
+    for (int g = 0; g < nbox; ++g) {
         for (int s = 0; s < S; ++s)
             if (nb[g * S + s] == -1 && trees[tree[g]]->bct[s] == 1) nmask[g] |= (unsigned char)(1u << s);
+        bflag[g] |= (unsigned char)(nmask[g] << BF_NSHIFT);  // kernels read it with the flags
+    }
 
     auto &own = owned;
     meta.nb = upload(nb, own);

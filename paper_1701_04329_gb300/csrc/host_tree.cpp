@@ -72,6 +72,30 @@ int HostTree::nfaces_of_leaf(int b) const {
     return n;
 }
 
+int HostTree::wrap(int a, int q, int side) const {
+    if (bct[2 * a] != 2) return q;
+    return ((q - 1) % side + side) % side + 1;
+}
+
+int HostTree::set_boundary_types(const int *types, std::string &err) {
+    bool any_dirichlet = false, change = false;
+    for (int s = 0; s < 2 * D; ++s) {
+        if (types[s] < 0 || types[s] > 2) { err = "unknown boundary type"; return -1; }
+        if ((types[s] == 2) != (types[s ^ 1] == 2)) { err = "periodic sides come in pairs (both sides of an axis)"; return -1; }
+        any_dirichlet |= types[s] == 0;
+        change |= (types[s] == 2) != (bct[s] == 2);
+    }
+    if (!any_dirichlet) { err = "at least one side must be Dirichlet (the problem is singular otherwise)"; return -1; }
+    if (change && boxes.size() != 1) { err = "periodic sides can only be switched while the tree is the root box"; return -1; }
+    bool same = true;
+    for (int s = 0; s < 2 * D; ++s) same &= bct[s] == types[s];
+    if (same) return 0;
+    for (int s = 0; s < 2 * D; ++s) bct[s] = types[s];
+    std::vector<HBox> pos = boxes;
+    rebuild(std::move(pos));  // neighbours (and the version) change
+    return 0;
+}
+
 void HostTree::rebuild(std::vector<HBox> &&pos) {
     for (auto &p : pos) {
         if (D == 2) p.idx[2] = 1;
@@ -109,7 +133,7 @@ void HostTree::rebuild(std::vector<HBox> &&pos) {
             dir_offset(d, off);
             bool inside = true;
             for (int a = 0; a < D; ++a) {
-                q[a] = b.idx[a] + off[a];
+                q[a] = wrap(a, b.idx[a] + off[a], side);
                 inside = inside && q[a] >= 1 && q[a] <= side;
             }
             b.nb[d] = inside ? find(b.level, q) : -2;
@@ -205,7 +229,7 @@ int HostTree::adapt(const int8_t *flags, int n_buf, int *n_added, int *n_removed
                 if (boxes[b].nb[d] != -1) continue;
                 int off[3], q[3] = {1, 1, 1};
                 dir_offset(d, off);
-                for (int a = 0; a < D; ++a) q[a] = (boxes[b].idx[a] + off[a] + 1) >> 1;
+                for (int a = 0; a < D; ++a) q[a] = (wrap(a, boxes[b].idx[a] + off[a], 1 << (l - 1)) + 1) >> 1;
                 const int c = find(l - 1, q);
                 if (c < 0 || !boxes[c].leaf()) { err = "adapt: tree not 2:1 balanced"; return -4; }
                 refine[c] = 1;

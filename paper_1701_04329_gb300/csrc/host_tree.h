@@ -34,7 +34,7 @@ class HostTree {
     std::vector<long long> leaf_face0; // first canonical boundary face of leaf i
     long long n_leaf_cells = 0, n_bfaces = 0;
     int version = 0;                   // bumped on every change
-    int bct[6] = {0, 0, 0, 0, 0, 0};   // per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann
+    int bct[6] = {0, 0, 0, 0, 0, 0};   // per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann, 2 periodic
 
     int ndir() const;                  // 3^D - 1
     int side_dir(int s) const;         // face side (-x,+x,-y,...) -> direction index
@@ -43,6 +43,10 @@ class HostTree {
     int nfaces_of_leaf(int b) const;
 
     int refine_uniform(int level, std::string &err);
+    // side types; periodicity (both sides of an axis) changes the connectivity and is
+    // accepted only while the tree is the root box alone
+    int set_boundary_types(const int *types, std::string &err);
+    int wrap(int a, int q, int side) const;  // index q on axis a, wrapped on a periodic axis
     int adapt(const int8_t *flags, int n_buf, int *n_added, int *n_removed, std::string &err);
 
   private:

@@ -24,6 +24,7 @@
 //   poff[b]      offset of this box's region in the parent, 8 bits per axis
 //   coff[b]      first cell of the box in every field array
 //   bcoff[b*2D+s] first Dirichlet value of side s (domain boundary sides)
+//   bflag[b]     bits 2..7: Neumann domain sides (bit 2 + s)
 //   bflag[b]     bit 0: refined (values are FAS coarse values); bit 1: has a
 //                side that is not a same-level neighbour
 //   tree[b]      tree of the box (batched forests); active[tree] masks trees
@@ -42,6 +43,7 @@ constexpr int kThreads = 256;
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr unsigned char BF_REFINED = 1, BF_SPECIAL = 2;
+constexpr int BF_NSHIFT = 2;  // flag bits 2..7: Neumann domain sides (bit 2 + s)
 
 struct BoxMeta {
     const int *nb;
@@ -67,7 +69,6 @@ struct BoxInfo {
     int b, flag, poff, parent;
     long long pcoff;  // cells of the parent (k_correct)
     int nmask;        // Neumann domain sides (of the parent in k_correct)
-    double h;         // cell size
 };
 
 // The activity mask is written by kernels: after pdl_wait, drop a prefetched
@@ -100,8 +101,7 @@ __device__ __forceinline__ void info_load(const BoxMeta &A, int idx, int n, int 
                 I.flag = A.bflag[b];
                 I.poff = A.poff[b];
                 I.parent = A.parent[b];
-                I.nmask = A.nmask[b];
-                I.h = A.hb[b];
+                I.nmask = I.flag >> BF_NSHIFT;
             }
         }
     }
@@ -301,7 +301,7 @@ __device__ __forceinline__ void gather(const BoxInfo &I, const T *__restrict__ u
 }
 
 template <int D, int M, typename T, int G>
-__device__ __forceinline__ void finalize(const BoxInfo &I, T *tile, int lt, int only) {
+__device__ __forceinline__ void finalize(const BoxInfo &I, T *tile, int lt, int only, const double *hb) {
     constexpr int F = Geo<D, M>::F;
     const int nf = only < 0 ? F : F / 2;
     for (int item = lt; item < 2 * D * nf; item += G) {
@@ -318,7 +318,7 @@ __device__ __forceinline__ void finalize(const BoxInfo &I, T *tile, int lt, int 
         face_pos(D, s, pin, t1, t2, i, j, k);
         const T u1 = tile[ti<D, M>(i, j, k)];
         if (code == -1) {  // the slot holds b: Dirichlet 2b - u_1, Neumann u_1 + h b
-            tile[gidx] = ((I.nmask >> s) & 1) ? fma(T(I.h), tile[gidx], u1) : T(2) * tile[gidx] - u1;
+            tile[gidx] = ((I.nmask >> s) & 1) ? fma(T(hb[I.b]), tile[gidx], u1) : T(2) * tile[gidx] - u1;
         } else {
             const T uH = tile[gidx];
             face_pos(D, s, p2, t1, t2, i, j, k);
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(BoxMeta A, int b0, int n, c
         }
         info_load<D>(A, base + stride + g, n, b0, list, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
-        if (special) finalize<D, M, T, S::G>(I, tile, lt, colour);
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, colour, A.hb);
         __syncthreads();
         if (b >= 0) {
 #pragma unroll
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxMeta A, int b0, 
         }
         info_load<D>(A, base + stride + g, n, b0, nullptr, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
-        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1, A.hb);
         __syncthreads();
         if (b >= 0) {
             const long long cp = A.coff[I.parent];
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
         }
         info_load<D>(A, base + stride + g, n, b0, nullptr, info[(buf ^ 1) * S::BPC + g], lt, S::G);
         __syncthreads();
-        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1, A.hb);
         __syncthreads();
         if (refined) {
             for (int v = lt; v < Gm::C / VEC; v += S::G) {
@@ -921,7 +921,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
             rm = pm = 0;
             cur = -1;
         }
-        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1);
+        if (special) finalize<D, M, T, S::G>(I, tile, lt, -1, A.hb);
         __syncthreads();
         if (b >= 0) {
             const T ih2 = T(ihb);

@@ -14,6 +14,8 @@
 // mode 1: the FMG steps l = lmin..1: store v'_l, correct from l-1 (l > lmin),
 //         V-cycle from l.
 #pragma once
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace afg {
@@ -56,24 +58,35 @@ __device__ __forceinline__ void bt_cell(int c, int col, int &i, int &j, int &k) 
 // g = 2b - u_1, Neumann (bit s of nm) g = u_1 + h b with h = 1/M (a bottom
 // box spans the domain); b = 0 for homogeneous data.  Face data: side s,
 // face cell t2 * M + t1 with (t1, t2) the tangential coordinates, x first.
-template <int D, int M, typename T>
+template <int D, int M, typename T, bool BC>
 __device__ __forceinline__ T bt_ghost(const T *bc, bool zero_b, int nm, int s, int t1, int t2, T self) {
     constexpr int F = D == 2 ? M : M * M;
     const T b = zero_b ? T(0) : bc[s * F + t2 * M + t1];
-    return ((nm >> s) & 1) ? fma(T(1) / T(M), b, self) : T(2) * b - self;
+    // g = a b + c u_1: (2, -1) Dirichlet, (h, 1) Neumann (2b and -u_1 are exact)
+    const bool neu = BC && ((nm >> s) & 1);
+    return fma(neu ? T(1) / T(M) : T(2), b, neu ? self : -self);
 }
 
-// ((x- + x+) + (y- + y+)) + (z- + z+) around interior cell (i,j,k), ghosts folded in
-template <int D, int M, typename T>
-__device__ __forceinline__ T bt_sum(const T *v, const T *bc, bool zero_b, int nm, int i, int j, int k, T self) {
-    const T xm = i > 0 ? v[pad_idx<D>(M, i - 1, j, k)] : bt_ghost<D, M, T>(bc, zero_b, nm, 0, j, k, self);
-    const T xp = i < M - 1 ? v[pad_idx<D>(M, i + 1, j, k)] : bt_ghost<D, M, T>(bc, zero_b, nm, 1, j, k, self);
-    const T ym = j > 0 ? v[pad_idx<D>(M, i, j - 1, k)] : bt_ghost<D, M, T>(bc, zero_b, nm, 2, i, k, self);
-    const T yp = j < M - 1 ? v[pad_idx<D>(M, i, j + 1, k)] : bt_ghost<D, M, T>(bc, zero_b, nm, 3, i, k, self);
+// ((x- + x+) + (y- + y+)) + (z- + z+) around interior cell (i,j,k), ghosts
+// folded in; on a periodic axis (bit a of pm) the box is its own neighbour,
+// so the value across the side is the cell at the other end of the row
+template <int D, int M, typename T, bool BC>
+__device__ __forceinline__ T bt_sum(const T *v, const T *bc, bool zero_b, int nm, int pm, int i, int j, int k,
+                                    T self) {
+    const T xm = i > 0 ? v[pad_idx<D>(M, i - 1, j, k)]
+                       : (BC && (pm & 1)) ? v[pad_idx<D>(M, M - 1, j, k)] : bt_ghost<D, M, T, BC>(bc, zero_b, nm, 0, j, k, self);
+    const T xp = i < M - 1 ? v[pad_idx<D>(M, i + 1, j, k)]
+                           : (BC && (pm & 1)) ? v[pad_idx<D>(M, 0, j, k)] : bt_ghost<D, M, T, BC>(bc, zero_b, nm, 1, j, k, self);
+    const T ym = j > 0 ? v[pad_idx<D>(M, i, j - 1, k)]
+                       : (BC && (pm & 2)) ? v[pad_idx<D>(M, i, M - 1, k)] : bt_ghost<D, M, T, BC>(bc, zero_b, nm, 2, i, k, self);
+    const T yp = j < M - 1 ? v[pad_idx<D>(M, i, j + 1, k)]
+                           : (BC && (pm & 2)) ? v[pad_idx<D>(M, i, 0, k)] : bt_ghost<D, M, T, BC>(bc, zero_b, nm, 3, i, k, self);
     T s = (xm + xp) + (ym + yp);
     if (D == 3) {
-        const T zm = k > 0 ? v[pad_idx<D>(M, i, j, k - 1)] : bt_ghost<D, M, T>(bc, zero_b, nm, 4, i, j, self);
-        const T zp = k < M - 1 ? v[pad_idx<D>(M, i, j, k + 1)] : bt_ghost<D, M, T>(bc, zero_b, nm, 5, i, j, self);
+        const T zm = k > 0 ? v[pad_idx<D>(M, i, j, k - 1)]
+                           : (BC && (pm & 4)) ? v[pad_idx<D>(M, i, j, M - 1)] : bt_ghost<D, M, T, BC>(bc, zero_b, nm, 4, i, j, self);
+        const T zp = k < M - 1 ? v[pad_idx<D>(M, i, j, k + 1)]
+                               : (BC && (pm & 4)) ? v[pad_idx<D>(M, i, j, 0)] : bt_ghost<D, M, T, BC>(bc, zero_b, nm, 5, i, j, self);
         s += zm + zp;
     }
     return s;
@@ -81,8 +94,8 @@ __device__ __forceinline__ T bt_sum(const T *v, const T *bc, bool zero_b, int nm
 
 // one barrier per half-sweep: the colour-c cells read only colour 1-c cells
 // and their own ghosts
-template <int D, int M, typename T>
-__device__ void bt_smooth(const BottomLevel &L, T *sm, int steps, int hom, int nm) {
+template <int D, int M, typename T, bool BC>
+__device__ void bt_smooth(const BottomLevel &L, T *sm, int steps, int hom, int nm, int pm) {
     constexpr int H = (D == 2 ? M * M : M * M * M) / 2;
     T *u = sm + L.ou;
     const T *rho = sm + L.orho, *bc = sm + L.obc;
@@ -93,7 +106,7 @@ __device__ void bt_smooth(const BottomLevel &L, T *sm, int steps, int hom, int n
                 int i, j, k;
                 bt_cell<D, M>(c, col, i, j, k);
                 const int p = pad_idx<D>(M, i, j, k);
-                const T sum = bt_sum<D, M, T>(u, bc, hom, nm, i, j, k, u[p]);
+                const T sum = bt_sum<D, M, T, BC>(u, bc, hom, nm, pm, i, j, k, u[p]);
                 u[p] = (sum - h2 * rho[(k * M + j) * M + i]) * inv;
             }
             __syncthreads();
@@ -102,8 +115,8 @@ __device__ void bt_smooth(const BottomLevel &L, T *sm, int steps, int hom, int n
 
 // residual of level L (box size M), restricted into the coarse level C (M/2,
 // same domain), then the coarse right-hand side
-template <int D, int M, typename T>
-__device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int hom, int nm) {
+template <int D, int M, typename T, bool BC>
+__device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int hom, int nm, int pm) {
     constexpr int MC = M / 2, CC = D == 2 ? MC * MC : MC * MC * MC;
     const T *u = sm + L.ou, *bcf = sm + L.obc;
     const T *rho = sm + L.orho;
@@ -121,13 +134,14 @@ __device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int h
                     su += uu;
                     sro += rho[(k * M + j) * M + i];
                     const int io = i + (dx ? 1 : -1), jo = j + (dy ? 1 : -1), ko = k + (dz ? 1 : -1);
+                    const int iw = (io + M) % M, jw = (jo + M) % M, kw = (ko + M) % M;  // periodic wrap
                     sout += (io >= 0 && io < M) ? u[pad_idx<D>(M, io, j, k)]
-                                                : bt_ghost<D, M, T>(bcf, hom, nm, dx, j, k, uu);
+                            : (BC && (pm & 1)) ? u[pad_idx<D>(M, iw, j, k)] : bt_ghost<D, M, T, BC>(bcf, hom, nm, dx, j, k, uu);
                     sout += (jo >= 0 && jo < M) ? u[pad_idx<D>(M, i, jo, k)]
-                                                : bt_ghost<D, M, T>(bcf, hom, nm, 2 + dy, i, k, uu);
+                            : (BC && (pm & 2)) ? u[pad_idx<D>(M, i, jw, k)] : bt_ghost<D, M, T, BC>(bcf, hom, nm, 2 + dy, i, k, uu);
                     if (D == 3)
                         sout += (ko >= 0 && ko < M) ? u[pad_idx<D>(M, i, j, ko)]
-                                                    : bt_ghost<D, M, T>(bcf, hom, nm, 4 + dz, i, j, uu);
+                                : (BC && (pm & 4)) ? u[pad_idx<D>(M, i, j, kw)] : bt_ghost<D, M, T, BC>(bcf, hom, nm, 4 + dz, i, j, uu);
                 }
         const T mu = su * w;
         uc[pad_idx<D>(MC, X, Y, Z)] = mu;
@@ -139,17 +153,18 @@ __device__ void bt_down(const BottomLevel &L, const BottomLevel &C, T *sm, int h
         int i, j, k;
         cell_of<D>(MC, c, i, j, k);
         const T uu = uc[pad_idx<D>(MC, i, j, k)];
-        rc[c] = fma(ihc2, fma(T(-2 * D), uu, bt_sum<D, MC, T>(uc, sm + C.obc, hom, nm, i, j, k, uu)), rc[c]);
+        rc[c] = fma(ihc2, fma(T(-2 * D), uu, bt_sum<D, MC, T, BC>(uc, sm + C.obc, hom, nm, pm, i, j, k, uu)), rc[c]);
     }
     __syncthreads();
 }
 
 // u_L += I (u_C - v'_C), 2-1-1 (2D) / 1-1-1-1 (3D); outside the box the
 // difference is the homogeneous ghost of the cell inside: -d across a
-// Dirichlet side, d across a Neumann side.
+// Dirichlet side, d across a Neumann side; across a periodic side it is the
+// difference at the other end of the row.
 // dc: scratch for the difference (padded, coarse size)
-template <int D, int M, typename T>
-__device__ void bt_correct(const BottomLevel &L, const BottomLevel &C, T *sm, T *dc, int nm) {
+template <int D, int M, typename T, bool BC>
+__device__ void bt_correct(const BottomLevel &L, const BottomLevel &C, T *sm, T *dc, int nm, int pm) {
     constexpr int MC = M / 2, CC = D == 2 ? MC * MC : MC * MC * MC, CL = D == 2 ? M * M : M * M * M;
     T *u = sm + L.ou;
     const T *uc = sm + C.ou, *vc = sm + C.ov;
@@ -166,14 +181,17 @@ __device__ void bt_correct(const BottomLevel &L, const BottomLevel &C, T *sm, T 
         const int X = i >> 1, Y = j >> 1, Z = k >> 1;
         const int xs = X + ((i & 1) ? 1 : -1), ys = Y + ((j & 1) ? 1 : -1), zs = Z + ((k & 1) ? 1 : -1);
         const T d0 = dc[pad_idx<D>(MC, X, Y, Z)];
-        auto outside = [&](int s) { return ((nm >> s) & 1) ? d0 : -d0; };
-        const T dx = (xs >= 0 && xs < MC) ? dc[pad_idx<D>(MC, xs, Y, Z)] : outside(xs < 0 ? 0 : 1);
-        const T dy = (ys >= 0 && ys < MC) ? dc[pad_idx<D>(MC, X, ys, Z)] : outside(ys < 0 ? 2 : 3);
+        auto outside = [&](int s) { return (BC && ((nm >> s) & 1)) ? d0 : -d0; };
+        const T dx = (xs >= 0 && xs < MC) ? dc[pad_idx<D>(MC, xs, Y, Z)]
+                     : (BC && (pm & 1)) ? dc[pad_idx<D>(MC, (xs + MC) % MC, Y, Z)] : outside(xs < 0 ? 0 : 1);
+        const T dy = (ys >= 0 && ys < MC) ? dc[pad_idx<D>(MC, X, ys, Z)]
+                     : (BC && (pm & 2)) ? dc[pad_idx<D>(MC, X, (ys + MC) % MC, Z)] : outside(ys < 0 ? 2 : 3);
         const int q = pad_idx<D>(M, i, j, k);
         if (D == 2) {
             u[q] = fma(T(0.25), dx + dy, fma(T(0.5), d0, u[q]));
         } else {
-            const T dz = (zs >= 0 && zs < MC) ? dc[pad_idx<D>(MC, X, Y, zs)] : outside(zs < 0 ? 4 : 5);
+            const T dz = (zs >= 0 && zs < MC) ? dc[pad_idx<D>(MC, X, Y, zs)]
+                         : (BC && (pm & 4)) ? dc[pad_idx<D>(MC, X, Y, (zs + MC) % MC)] : outside(zs < 0 ? 4 : 5);
             u[q] = fma(T(0.25), ((d0 + dx) + dy) + dz, u[q]);
         }
     }
@@ -189,19 +207,19 @@ __device__ void bt_correct(const BottomLevel &L, const BottomLevel &C, T *sm, T 
         default: { constexpr int MB = 16; CALL; break; }    \
     }
 
-template <int D, typename T>
+template <int D, typename T, bool BC>
 __device__ void bt_vcycle(const BottomLevel *Ls, int lmin, int ltop, T *sm, T *dc, int nd, int nu, int nb, int hom,
-                          int nm) {
+                          int nm, int pm) {
     for (int l = ltop; l > lmin; --l) {
         const int li = l - lmin;
-        AFG_BT_M(li, (bt_smooth<D, MB, T>(Ls[li], sm, nd, hom, nm)));
-        AFG_BT_M(li, (bt_down<D, MB, T>(Ls[li], Ls[li - 1], sm, hom, nm)));
+        AFG_BT_M(li, (bt_smooth<D, MB, T, BC>(Ls[li], sm, nd, hom, nm, pm)));
+        AFG_BT_M(li, (bt_down<D, MB, T, BC>(Ls[li], Ls[li - 1], sm, hom, nm, pm)));
     }
-    bt_smooth<D, 2, T>(Ls[0], sm, nb, hom, nm);
+    bt_smooth<D, 2, T, BC>(Ls[0], sm, nb, hom, nm, pm);
     for (int l = lmin + 1; l <= ltop; ++l) {
         const int li = l - lmin;
-        AFG_BT_M(li, (bt_correct<D, MB, T>(Ls[li], Ls[li - 1], sm, dc, nm)));
-        AFG_BT_M(li, (bt_smooth<D, MB, T>(Ls[li], sm, nu, hom, nm)));
+        AFG_BT_M(li, (bt_correct<D, MB, T, BC>(Ls[li], Ls[li - 1], sm, dc, nm, pm)));
+        AFG_BT_M(li, (bt_smooth<D, MB, T, BC>(Ls[li], sm, nu, hom, nm, pm)));
     }
 }
 
@@ -239,6 +257,8 @@ __global__ void __launch_bounds__(kThreads) k_bottom(BoxMeta A, int ntrees, int 
     pdl_wait();
     if (A.active && !A.active[t]) return;  // uniform per CTA: no barrier has been passed yet
     const int nm = A.nmask[b0s[nl - 1] + t];  // Neumann sides (the same for every box below the root)
+    int pm = 0;  // periodic axes: the root box is its own neighbour there
+    for (int a = 0; a < D; ++a) pm |= (A.nb[(b0s[nl - 1] + t) * 2 * D + 2 * a] >= 0) << a;
     // stage
     for (int li = 0; li < nl; ++li) {
         const BottomLevel &L = Ls[li];
@@ -255,30 +275,38 @@ __global__ void __launch_bounds__(kThreads) k_bottom(BoxMeta A, int ntrees, int 
         const int F = D == 2 ? L.M : L.M * L.M;
         for (int x = threadIdx.x; x < L.faces; x += blockDim.x) {
             const int s = x / F, f = x % F;
-            sm[L.obc + x] = hom ? T(0) : T(A.bc[A.nbase[b * 2 * D + s] + f]);
+            // face data exists on domain-boundary sides only (a periodic side's offset is a cell offset)
+            const bool phys = A.nb[b * 2 * D + s] == -1;
+            sm[L.obc + x] = (hom || !phys) ? T(0) : T(A.bc[A.nbase[b * 2 * D + s] + f]);
         }
     }
     __syncthreads();
-    if (mode == 0) {
-        bt_vcycle<D, T>(Ls, lmin, ltop, sm, dc, nd, nu, nb, hom, nm);
-    } else {
-        for (int l = lmin; l <= 1; ++l) {
-            const BottomLevel &L = Ls[l - lmin];
-            for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
-                int i, j, k;
-                cell_of<D>(L.M, c, i, j, k);
-                const int p = pad_idx<D>(L.M, i, j, k);
-                sm[L.ov + p] = sm[L.ou + p];
+    auto run = [&](auto bc) {
+        constexpr bool BC = decltype(bc)::value;
+        if (mode == 0) {
+            bt_vcycle<D, T, BC>(Ls, lmin, ltop, sm, dc, nd, nu, nb, hom, nm, pm);
+        } else {
+            for (int l = lmin; l <= 1; ++l) {
+                const BottomLevel &L = Ls[l - lmin];
+                for (int c = threadIdx.x; c < L.cells; c += blockDim.x) {
+                    int i, j, k;
+                    cell_of<D>(L.M, c, i, j, k);
+                    const int p = pad_idx<D>(L.M, i, j, k);
+                    sm[L.ov + p] = sm[L.ou + p];
+                }
+                __syncthreads();
+                if (l > lmin) {
+                    // the FMG correction uses the copy stored at the start of step l-1
+                    const int li = l - lmin;
+                    AFG_BT_M(li, (bt_correct<D, MB, T, BC>(L, Ls[li - 1], sm, dc, nm, pm)));
+                }
+                bt_vcycle<D, T, BC>(Ls, lmin, l, sm, dc, nd, nu, nb, hom, nm, pm);
             }
-            __syncthreads();
-            if (l > lmin) {
-                // the FMG correction uses the copy stored at the start of step l-1
-                const int li = l - lmin;
-                AFG_BT_M(li, (bt_correct<D, MB, T>(L, Ls[li - 1], sm, dc, nm)));
-            }
-            bt_vcycle<D, T>(Ls, lmin, l, sm, dc, nd, nu, nb, hom, nm);
         }
-    }
+    };
+    // all-Dirichlet trees take the plain instance (uniform per CTA)
+    if (nm | pm) run(std::true_type{});
+    else run(std::false_type{});
     // write back
     for (int li = 0; li < nl; ++li) {
         const BottomLevel &L = Ls[li];

@@ -135,7 +135,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
             const T u1 = gv;
             if (code == -1) {
                 const T bv = hom ? T(0) : T(A.bc[I.base[s] + k * M + j]);
-                gv = ((I.nmask >> s) & 1) ? fma(T(I.h), bv, u1) : T(2) * bv - u1;
+                gv = ((I.nmask >> s) & 1) ? fma(T(A.hb[I.b]), bv, u1) : T(2) * bv - u1;
             } else {
                 const int iin = s ? M - 1 : 0, p2 = s ? M - 2 : 1;
                 const int cj = unpack_off(I.poff, 1) + (j >> 1);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
                 if (code == -1) {
                     const int t2 = a == 1 ? kin : jin;
                     const T bv = hom ? T(0) : T(A.bc[I.base[s] + t2 * M + i]);
-                    gv[x] = ((I.nmask >> s) & 1) ? fma(T(I.h), bv, u1) : T(2) * bv - u1;
+                    gv[x] = ((I.nmask >> s) & 1) ? fma(T(A.hb[I.b]), bv, u1) : T(2) * bv - u1;
                 } else {
                     const int ci = unpack_off(I.poff, 0) + (i >> 1);
                     int cj, ck;

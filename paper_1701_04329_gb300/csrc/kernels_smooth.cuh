@@ -184,8 +184,9 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
             T &gv = X[s * S::ROWS + sp_row<D, M>(j, k)];
             const T u1 = gv;
             if (code == -1) {
+                if ((I.nmask >> s) & 1) continue;  // Neumann: the pass below
                 const T bv = hom ? T(0) : T(A.bc[I.base[s] + k * M + j]);
-                gv = ((I.nmask >> s) & 1) ? fma(T(I.h), bv, u1) : T(2) * bv - u1;
+                gv = T(2) * bv - u1;
             } else {
                 const int iin = s ? M - 1 : 0, p2 = s ? M - 2 : 1;
                 const int cj = unpack_off(I.poff, 1) + (j >> 1);
@@ -210,8 +211,9 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
                 const T u1 = gv[x];
                 if (code == -1) {
                     const int t2 = a == 1 ? kin : jin;
+                    if ((I.nmask >> s) & 1) continue;  // Neumann: the pass below
                     const T bv = hom ? T(0) : T(A.bc[I.base[s] + t2 * M + i]);
-                    gv[x] = ((I.nmask >> s) & 1) ? fma(T(I.h), bv, u1) : T(2) * bv - u1;
+                    gv[x] = T(2) * bv - u1;
                 } else {
                     const int ci = unpack_off(I.poff, 0) + (i >> 1);
                     int cj, ck;
@@ -233,11 +235,37 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
             }
         }
     }
+    if (!I.nmask) return;
+    // Neumann domain sides: g = u_1 + h b (a separate pass keeps the common path lean)
+    const T hbox = T(A.hb[I.b]);
+    for (int item = lt; item < S::NGI; item += S::G) {
+        if (item < 2 * S::NXI) {
+            int s, j, k;
+            sp_xitem<D, M>(item, c, s, j, k);
+            if (I.code[s] != -1 || !((I.nmask >> s) & 1)) continue;
+            T &gv = X[s * S::ROWS + sp_row<D, M>(j, k)];
+            const T bv = hom ? T(0) : T(A.bc[I.base[s] + k * M + j]);
+            gv = fma(hbox, bv, gv);
+        } else {
+            int s, h0, jg, kg, jin, kin, jm, km;
+            sp_yzitem<D, M, T>(item - 2 * S::NXI, s, h0, jg, kg, jin, kin, jm, km);
+            if (I.code[s] != -1 || !((I.nmask >> s) & 1)) continue;
+            T *gv = P + sp_row<D, M>(jg, kg) * MH + h0;
+            const int rg = (c + jin + kin + D) & 1;
+            const int t2 = (s >> 1) == 1 ? kin : jin;
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) {
+                const int i = 2 * (h0 + x) + rg;
+                const T bv = hom ? T(0) : T(A.bc[I.base[s] + t2 * M + i]);
+                gv[x] = fma(hbox, bv, gv[x]);
+            }
+        }
+    }
 }
 
 // scaled = 1: rho holds -h^2 rho / (2D) and the update is u = sum/(2D) + rho
 template <int D, int M, typename T>
-__global__ void __launch_bounds__(kThreads) k_smooth_p(BoxMeta A, int b0, int n, const int *list, T *u,
+__global__ void __launch_bounds__(kThreads, 6) k_smooth_p(BoxMeta A, int b0, int n, const int *list, T *u,
                                                        const T *__restrict__ rho, T h2, int colour, int hom,
                                                        int scaled) {
     using S = SpCfg<D, M, T>;

@@ -70,3 +70,23 @@ def test_boundary_types_validated_on_the_host():
         assert False
     except ValueError:
         pass
+
+
+def test_periodic_types_validated_on_the_host():
+    """Periodic sides come in pairs and switch only on the root box alone."""
+    t = afgpu.Tree(3, 8, 4)
+    for bad in ([2, 0, 0, 0, 0, 0], [2, 2, 2, 2, 2, 2], [2, 2, 1, 1, 2, 2]):
+        try:
+            t.set_boundary_types(bad)
+            assert False, bad
+        except afgpu.AfgError as e:
+            assert e.code == afgpu.AFG_ERR_ARG
+    t.set_boundary_types([afgpu.AFG_BC_PERIODIC] * 2 + [afgpu.AFG_BC_DIRICHLET] * 4)
+    t.refine_uniform(2)
+    try:
+        t.set_boundary_types([0] * 6)
+        assert False
+    except afgpu.AfgError as e:
+        assert e.code == afgpu.AFG_ERR_ARG
+    t.set_boundary_types([2, 2, 1, 0, 0, 0])  # Neumann/Dirichlet changes stay allowed
+    assert t.n_bfaces == 4 * 4 * 64  # no boundary faces on the periodic x sides

@@ -52,3 +52,26 @@ def test_workload_trees(make):
     p.build(a)
     p.build(b)
     same_tree(a, b)
+
+
+@pytest.mark.parametrize("D,N,seed,types", [(2, 4, 11, [2, 2, 0, 0]), (2, 8, 12, [0, 1, 2, 2]),
+                                            (3, 4, 13, [2, 2, 0, 0, 2, 2]), (3, 8, 14, [2, 2, 2, 2, 0, 1])])
+def test_periodic_adapt_sequences(D, N, seed, types):
+    """Periodic sides (Sec. 2.2: wrapped connectivity): both builders agree
+    bit for bit, including 2:1 refinement across the wrapped sides."""
+    rng = np.random.default_rng(seed)
+    maxl = 6 if D == 2 else 4
+    a, b = OracleTree(D, N, maxl), afgpu.Tree(D, N, maxl)
+    for t in (a, b):
+        t.set_boundary_types(types)
+        t.refine_uniform(2)
+    periodic = tuple(x for x in range(D) if types[2 * x] == 2)
+    for step in range(5):
+        n = a.n_leaf_cells
+        assert n == b.n_leaf_cells
+        flags = rng.choice(np.array([-1, 0, 1], np.int8), size=n, p=[0.4, 0.5, 0.1])
+        flags[np.repeat(rng.random(n // N ** D) < 0.4, N ** D)] = -1
+        nbuf = int(rng.integers(0, 3))
+        assert a.adapt(flags, nbuf) == b.adapt(flags, nbuf)
+        check_tree(same_tree(a, b), D, periodic=periodic)
+    assert len(a.face_centers()) == b.n_bfaces
