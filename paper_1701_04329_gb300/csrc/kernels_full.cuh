@@ -459,7 +459,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual_p(BoxMeta A, const i
 // the domain boundary, where the difference changes sign on Dirichlet sides
 // and keeps it on Neumann sides) arrive by cp.async
 // one box ahead; d = v_H - v'_H is formed once per staged value, then the
-// 2-1-1 / 1-1-1-1 prolongation (Sec. 2.5) is added.
+// 2-1-1 / 1-1-1-1 prolongation (Sec. 2.5) is added.  In 3D the prolongation
+// of child (sx,sy,sz) is (1/4)((d0 + d_x(sx)) + (d_y(sy) + d_z(sz))): the two
+// x-pair and four yz-pair sums of a coarse cell are formed once for its 8
+// children (2.75 instead of 4 additions per fine cell; it matters for FP64,
+// whose arithmetic bounds this kernel).
 // ---------------------------------------------------------------------------
 template <int D, int M, typename T>
 struct CpCfg {
@@ -472,7 +476,10 @@ struct CpCfg {
     static constexpr int G = NV < kThreads ? NV : kThreads;
     static constexpr int BPC = kThreads / G;
     static constexpr int NIT = (NV + G - 1) / G;
-    static constexpr int BOX = C + 2 * QCP;
+    // 3D: the pair sums of each coarse cell, shared by its 8 children
+    static constexpr int N3 = MH * MH * MH;
+    static constexpr int PSZ = D == 3 ? (6 * N3 + VEC - 1) / VEC * VEC : 0;
+    static constexpr int BOX = C + 2 * QCP + PSZ;
     static constexpr int NST = 2;
     static constexpr bool ok = MH >= VEC;  // a vector stays inside one half-row
     static constexpr size_t smem() { return sizeof(T) * BOX * BPC * NST + sizeof(BoxInfo) * BPC * (NST + 1); }
@@ -576,6 +583,25 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
             }
         }
         __syncthreads();
+        // 3D: a child (sx,sy,sz) of coarse cell X gets (1/4)((d0 + d_x(sx)) + (d_y(sy) + d_z(sz))):
+        // the 2 x-pair and 4 yz-pair sums of a coarse cell are formed once for its 8 children
+        T *PS = st + S::C + 2 * S::QCP;
+        if constexpr (D == 3) {
+            if (I.b >= 0) {
+                for (int c = lt; c < S::N3; c += S::G) {
+                    const int X = c % MH, Y = (c / MH) % MH, Z = c / (MH * MH);
+                    const int b = ((Z + 1) * Q + (Y + 1)) * Q + (X + 1);
+                    const T d0 = DU[b], dym = DU[b - Q], dyp = DU[b + Q], dzm = DU[b - Q * Q], dzp = DU[b + Q * Q];
+                    PS[c] = d0 + DU[b - 1];
+                    PS[S::N3 + c] = d0 + DU[b + 1];
+                    PS[2 * S::N3 + c] = dym + dzm;
+                    PS[3 * S::N3 + c] = dym + dzp;
+                    PS[4 * S::N3 + c] = dyp + dzm;
+                    PS[5 * S::N3 + c] = dyp + dzp;
+                }
+            }
+            __syncthreads();
+        }
         if (I.b >= 0) {
 #pragma unroll
             for (int itv = 0; itv < S::NIT; ++itv) {
@@ -591,11 +617,20 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
                 const int b = D == 2 ? ((j >> 1) + 1) * Q + (h0 + 1) : (((k >> 1) + 1) * Q + ((j >> 1) + 1)) * Q + (h0 + 1);
                 T uv[VEC], res[VEC];
                 ldv<T, VEC>(U + v * VEC, uv);
+                if constexpr (D == 3) {
+                    const int c0 = ((k >> 1) * MH + (j >> 1)) * MH + h0;
+                    const T *px = PS + (r ? S::N3 : 0) + c0;
+                    const T *qyz = PS + (2 + 2 * (j & 1) + (k & 1)) * S::N3 + c0;
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const T d0 = DU[b + e], dx = DU[b + e + ox], dy = DU[b + e + oy];
-                    if (D == 2) res[e] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uv[e]));
-                    else res[e] = fma(T(0.25), ((d0 + dx) + dy) + DU[b + e + oz], uv[e]);
+                    for (int e = 0; e < VEC; ++e) res[e] = fma(T(0.25), px[e] + qyz[e], uv[e]);
+                    (void)oz;
+                    (void)b;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const T d0 = DU[b + e], dx = DU[b + e + ox], dy = DU[b + e + oy];
+                        res[e] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uv[e]));
+                    }
                 }
                 stv<T, VEC>(u + I.coff + (long long)v * VEC, res);
             }

@@ -111,8 +111,8 @@ void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, 
 template <int D, int M, int MP, typename T>
 void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     if (n <= 0) return;
-    // FP32: staged copies (the FP64 correction is bound by its FP64 additions either way)
-    if constexpr (CpCfg<D, M, T>::ok && sizeof(T) == 4) {
+    // staged copies; in 3D the pair sums of a coarse cell are shared by its children
+    if constexpr (CpCfg<D, M, T>::ok) {
         using S = CpCfg<D, M, T>;
         const size_t smem = S::smem();
         auto k = k_correct_p<D, M, MP, T>;
