@@ -31,6 +31,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "fxsum.cuh"
 
 namespace afg {
 
@@ -415,13 +416,76 @@ struct FullCfg {
     }
 };
 
-// sum of the 2D face neighbours of tile slot t, ((x-+x+)+(y-+y+))+(z-+z+)
+// FP64 neighbour sums: the first kFxTerms terms of ((x-+x+)+(y-+y+))+(z-+z+)
+// are summed exactly on the integer pipe (fxsum.cuh, one rounding), the others
+// are added to that partial sum in FP64.  GB300's integer ALU pipe is not
+// free either, so the split balances it against the FP64 pipe; every split is
+// at least as accurate as FP64 addition throughout.  FP32 sums use the FP32
+// adders.
+constexpr int kFxTerms = 4;
+
+template <int D, typename T>
+__device__ __forceinline__ T nb_sum_fp(const T (&x)[2 * D]) {
+    T s = (x[0] + x[1]) + (x[2] + x[3]);
+    if (D == 3) s += x[4] + x[5];
+    return s;
+}
+
+// sum of the 2D face neighbours x[0..2D-1] (order -x,+x,-y,+y,-z,+z)
+template <int D, typename T>
+__device__ __forceinline__ T nb_sum_x(const T (&x)[2 * D]) {
+    constexpr int K = kFxTerms < 2 * D ? kFxTerms : 2 * D;
+    if constexpr (K > 0 && sizeof(T) == 8) {
+        double p;
+        if (fx_sum<K>(x, 0.0, p)) {
+#pragma unroll
+            for (int k = K; k < 2 * D; ++k) p += x[k];
+            return p;
+        }
+    }
+    return nb_sum_fp<D, T>(x);
+}
+
+// the same less 2D times the centre value c: h^2 times the operator of Eq. 5
+template <int D, typename T>
+__device__ __forceinline__ T nb_lap_x(T c, const T (&x)[2 * D]) {
+    if constexpr (kFxTerms >= 2 * D && sizeof(T) == 8) {
+        double s;
+        if (fx_sum<2 * D, 2 * D>(x, c, s)) return s;
+    }
+    return fma(T(-2 * D), c, nb_sum_x<D, T>(x));
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T nb_sum6(T xm, T xp, T ym, T yp, T zm, T zp) {
+    T x[2 * D];
+    x[0] = xm; x[1] = xp; x[2] = ym; x[3] = yp;
+    if constexpr (D == 3) { x[4] = zm; x[5] = zp; }
+    return nb_sum_x<D, T>(x);
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T nb_lap6(T c, T xm, T xp, T ym, T yp, T zm, T zp) {
+    T x[2 * D];
+    x[0] = xm; x[1] = xp; x[2] = ym; x[3] = yp;
+    if constexpr (D == 3) { x[4] = zm; x[5] = zp; }
+    return nb_lap_x<D, T>(c, x);
+}
+
+// sum of the 2D face neighbours of tile slot t
 template <int D, int M, typename T>
 __device__ __forceinline__ T nb_sum_t(const T *tile, int t) {
     constexpr int P = M + 2;
-    T s = (tile[t - 1] + tile[t + 1]) + (tile[t - P] + tile[t + P]);
-    if (D == 3) s += tile[t - P * P] + tile[t + P * P];
-    return s;
+    return nb_sum6<D, T>(tile[t - 1], tile[t + 1], tile[t - P], tile[t + P], D == 3 ? tile[t - P * P] : T(0),
+                         D == 3 ? tile[t + P * P] : T(0));
+}
+
+// the same less 2D times the value of slot t
+template <int D, int M, typename T>
+__device__ __forceinline__ T nb_lap_t(const T *tile, int t) {
+    constexpr int P = M + 2;
+    return nb_lap6<D, T>(tile[t], tile[t - 1], tile[t + 1], tile[t - P], tile[t + P],
+                         D == 3 ? tile[t - P * P] : T(0), D == 3 ? tile[t + P * P] : T(0));
 }
 
 // shared-memory carve-up: tiles, then the double-buffered BoxInfo, then tables
@@ -634,7 +698,7 @@ __global__ void __launch_bounds__(kThreads) k_fas(BoxMeta A, int b0, int n, cons
                 for (int x = 0; x < VEC; ++x) {
                     const int q = v * VEC + x;
                     const int t = tix[q];
-                    out[x] = fma(ih2, fma(T(-2 * D), tile[t], nb_sum_t<D, M, T>(tile, t)), R[q]);
+                    out[x] = fma(ih2, nb_lap_t<D, M, T>(tile, t), R[q]);
                 }
                 stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
                 if (rhoh) {
@@ -933,7 +997,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual(BoxMeta A, const int
                     const int t = tix[q];
                     // r = rho - (sum - 2D u) / h^2 as two FMAs; |.| on the bit patterns
                     // (integer pipe), so the FP64 pipe only sees the stencil
-                    const T lap = fma(T(-2 * D), tile[t], nb_sum_t<D, M, T>(tile, t));
+                    const T lap = nb_lap_t<D, M, T>(tile, t);
                     const T rr = fma(-ih2, lap, RH[q]);
                     out[x] = R(rr);
                     rm = max(rm, abs_bits(rr));

@@ -185,17 +185,17 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
     }
 }
 
-// For the VEC cells of colour col at half-row (j,k), h0..h0+VEC-1: their
-// values and the sums of their 2D neighbours, ((x-+x+)+(y-+y+))+(z-+z+).
+// For the VEC cells of colour col at half-row (j,k), h0..h0+VEC-1: the sums
+// of their 2D neighbours less 2D times their own values (h^2 A u, Eq. 5).
 template <int D, int M, typename T>
-__device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, int h0, T *self, T *sum) {
+__device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, int h0, T *lap) {
     using F = FpCfg<D, M, T>;
     constexpr int VEC = F::VEC, MH = F::MH;
     const int rowi = sp_row<D, M>(j, k);
     const int r = (col + j + k + D) & 1;  // cells at i = 2h + r; neighbours in the other plane
     const T *po = st + (1 - col) * F::PT + rowi * MH + h0;
     const T *X = st + 2 * F::PT;
-    T xv[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
+    T self[VEC], xv[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC];
     ldv<T, VEC>(st + col * F::PT + rowi * MH + h0, self);
     ldv<T, VEC>(po, xv);
     T extra;
@@ -211,9 +211,7 @@ __device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, i
     for (int x = 0; x < VEC; ++x) {
         const T xl = r ? xv[x] : (x ? xv[x - 1] : extra);
         const T xr = r ? (x + 1 < VEC ? xv[x + 1] : extra) : xv[x];
-        T s = (xl + xr) + (ym[x] + yp[x]);
-        if (D == 3) s += zm[x] + zp[x];
-        sum[x] = s;
+        lap[x] = nb_lap6<D, T>(self[x], xl, xr, ym[x], yp[x], D == 3 ? zm[x] : T(0), D == 3 ? zp[x] : T(0));
     }
 }
 
@@ -358,11 +356,11 @@ __global__ void __launch_bounds__(kThreads) k_fas_p(BoxMeta A, int b0, int n, co
             const int col = v / NVH, w = v % NVH;
             const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
             const int j = row % M, k = D == 2 ? 0 : row / M;
-            T self[VEC], sum[VEC], rv[VEC], out[VEC];
-            fp_lap_vec<D, M, T>(st, col, j, k, h0, self, sum);
+            T lap[VEC], rv[VEC], out[VEC];
+            fp_lap_vec<D, M, T>(st, col, j, k, h0, lap);
             ldv<T, VEC>(FL + v * VEC, rv);
 #pragma unroll
-            for (int x = 0; x < VEC; ++x) out[x] = fma(ih2, fma(T(-2 * D), self[x], sum[x]), rv[x]);
+            for (int x = 0; x < VEC; ++x) out[x] = fma(ih2, lap[x], rv[x]);
             stv<T, VEC>(rho + I.coff + (long long)v * VEC, out);
             if (rhoh) {
 #pragma unroll
@@ -418,14 +416,14 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual_p(BoxMeta A, const i
             const int col = v / NVH, w = v % NVH;
             const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
             const int j = row % M, k = D == 2 ? 0 : row / M;
-            T self[VEC], sum[VEC], rv[VEC];
-            fp_lap_vec<D, M, T>(st, col, j, k, h0, self, sum);
+            T lap[VEC], rv[VEC];
+            fp_lap_vec<D, M, T>(st, col, j, k, h0, lap);
             ldv<T, VEC>(FL + v * VEC, rv);
             R out[VEC];
 #pragma unroll
             for (int x = 0; x < VEC; ++x) {
-                // r = rho - (sum - 2D u) / h^2 as two FMAs; |.| on the bit patterns
-                const T rr = fma(-ih2, fma(T(-2 * D), self[x], sum[x]), rv[x]);
+                // r = rho - (sum - 2D u) / h^2; |.| on the bit patterns
+                const T rr = fma(-ih2, lap[x], rv[x]);
                 out[x] = R(rr);
                 rm = max(rm, abs_bits(rr));
                 pm = max(pm, abs_bits(rv[x]));

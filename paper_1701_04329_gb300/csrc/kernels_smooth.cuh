@@ -263,9 +263,12 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
     }
 }
 
+// resident blocks per SM the register allocation must allow (FP32 / FP64)
+constexpr int kSmoothMinBlocks32 = 6, kSmoothMinBlocks64 = 6;
+
 // scaled = 1: rho holds -h^2 rho / (2D) and the update is u = sum/(2D) + rho
 template <int D, int M, typename T>
-__global__ void __launch_bounds__(kThreads, 6) k_smooth_p(BoxMeta A, int b0, int n, const int *list, T *u,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 : kSmoothMinBlocks64) k_smooth_p(BoxMeta A, int b0, int n, const int *list, T *u,
                                                        const T *__restrict__ rho, T h2, int colour, int hom,
                                                        int scaled) {
     using S = SpCfg<D, M, T>;
@@ -339,8 +342,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_smooth_p(BoxMeta A, int b0, int
                 for (int x = 0; x < VEC; ++x) {
                     const T xl = r ? xv[x] : (x ? xv[x - 1] : extra);
                     const T xr = r ? (x + 1 < VEC ? xv[x + 1] : extra) : xv[x];
-                    T sum = (xl + xr) + (ym[x] + yp[x]);
-                    if (D == 3) sum += zm[x] + zp[x];
+                    const T sum = nb_sum6<D, T>(xl, xr, ym[x], yp[x], D == 3 ? zm[x] : T(0), D == 3 ? zp[x] : T(0));
                     out[x] = scaled ? fma(sum, inv, rv[x]) : (sum - h2 * rv[x]) * inv;
                 }
                 stv<T, VEC>(u + I.coff + c * H + v * VEC, out);

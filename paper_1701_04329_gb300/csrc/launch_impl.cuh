@@ -13,6 +13,8 @@
 
 namespace afg {
 
+// FP64 half-sweeps: the staged half-row kernel (true) or the table-driven one
+constexpr bool kStagedSmooth64 = true;
 
 int sm_count();
 // resident CTAs per SM of a kernel for a given dynamic shared memory size (cached)
@@ -50,9 +52,9 @@ template <int D, int M, typename T>
 void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
                const void *rhoh, double h2, int colour, int hom) {
     if (n <= 0) return;
-    // FP32: the staged half-row kernel; FP64 keeps the table-driven one (FP64-issue bound,
-    // it keeps 8 blocks per SM: 0.123 vs 0.142 ms on 256^3)
-    if constexpr (SpCfg<D, M, T>::ok && sizeof(T) == 4) {
+    // FP32: the staged half-row kernel; FP64 keeps the table-driven one unless
+    // kStagedSmooth64 is set
+    if constexpr (SpCfg<D, M, T>::ok && (sizeof(T) == 4 || kStagedSmooth64)) {
         {
             using S = SpCfg<D, M, T>;
             const size_t smem = S::smem();
