@@ -264,7 +264,7 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
 }
 
 // resident blocks per SM the register allocation must allow (FP32 / FP64)
-constexpr int kSmoothMinBlocks32 = 6, kSmoothMinBlocks64 = 6;
+constexpr int kSmoothMinBlocks32 = 6, kSmoothMinBlocks64 = 5;
 
 // scaled = 1: rho holds -h^2 rho / (2D) and the update is u = sum/(2D) + rho
 template <int D, int M, typename T>
