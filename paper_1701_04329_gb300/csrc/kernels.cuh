@@ -431,10 +431,11 @@ __device__ __forceinline__ T nb_sum_fp(const T (&x)[2 * D]) {
     return s;
 }
 
-// sum of the 2D face neighbours x[0..2D-1] (order -x,+x,-y,+y,-z,+z)
-template <int D, typename T>
+// sum of the 2D face neighbours x[0..2D-1] (order -x,+x,-y,+y,-z,+z); FX =
+// false keeps FP64 adds (for kernels where the integer path costs registers)
+template <int D, typename T, bool FX = true>
 __device__ __forceinline__ T nb_sum_x(const T (&x)[2 * D]) {
-    constexpr int K = kFxTerms < 2 * D ? kFxTerms : 2 * D;
+    constexpr int K = !FX ? 0 : kFxTerms < 2 * D ? kFxTerms : 2 * D;
     if constexpr (K > 0 && sizeof(T) == 8) {
         double p;
         if (fx_sum<K>(x, 0.0, p)) {
@@ -447,13 +448,13 @@ __device__ __forceinline__ T nb_sum_x(const T (&x)[2 * D]) {
 }
 
 // the same less 2D times the centre value c: h^2 times the operator of Eq. 5
-template <int D, typename T>
+template <int D, typename T, bool FX = true>
 __device__ __forceinline__ T nb_lap_x(T c, const T (&x)[2 * D]) {
-    if constexpr (kFxTerms >= 2 * D && sizeof(T) == 8) {
+    if constexpr (FX && kFxTerms >= 2 * D && sizeof(T) == 8) {
         double s;
         if (fx_sum<2 * D, 2 * D>(x, c, s)) return s;
     }
-    return fma(T(-2 * D), c, nb_sum_x<D, T>(x));
+    return fma(T(-2 * D), c, nb_sum_x<D, T, FX>(x));
 }
 
 template <int D, typename T>
@@ -464,12 +465,12 @@ __device__ __forceinline__ T nb_sum6(T xm, T xp, T ym, T yp, T zm, T zp) {
     return nb_sum_x<D, T>(x);
 }
 
-template <int D, typename T>
+template <int D, typename T, bool FX = true>
 __device__ __forceinline__ T nb_lap6(T c, T xm, T xp, T ym, T yp, T zm, T zp) {
     T x[2 * D];
     x[0] = xm; x[1] = xp; x[2] = ym; x[3] = yp;
     if constexpr (D == 3) { x[4] = zm; x[5] = zp; }
-    return nb_lap_x<D, T>(c, x);
+    return nb_lap_x<D, T, FX>(c, x);
 }
 
 // sum of the 2D face neighbours of tile slot t

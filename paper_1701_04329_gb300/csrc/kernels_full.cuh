@@ -187,7 +187,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
 
 // For the VEC cells of colour col at half-row (j,k), h0..h0+VEC-1: the sums
 // of their 2D neighbours less 2D times their own values (h^2 A u, Eq. 5).
-template <int D, int M, typename T>
+template <int D, int M, typename T, bool FX = true>
 __device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, int h0, T *lap) {
     using F = FpCfg<D, M, T>;
     constexpr int VEC = F::VEC, MH = F::MH;
@@ -211,7 +211,7 @@ __device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, i
     for (int x = 0; x < VEC; ++x) {
         const T xl = r ? xv[x] : (x ? xv[x - 1] : extra);
         const T xr = r ? (x + 1 < VEC ? xv[x + 1] : extra) : xv[x];
-        lap[x] = nb_lap6<D, T>(self[x], xl, xr, ym[x], yp[x], D == 3 ? zm[x] : T(0), D == 3 ? zp[x] : T(0));
+        lap[x] = nb_lap6<D, T, FX>(self[x], xl, xr, ym[x], yp[x], D == 3 ? zm[x] : T(0), D == 3 ? zp[x] : T(0));
     }
 }
 
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_fas_p(BoxMeta A, int b0, int n, co
             const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
             const int j = row % M, k = D == 2 ? 0 : row / M;
             T lap[VEC], rv[VEC], out[VEC];
-            fp_lap_vec<D, M, T>(st, col, j, k, h0, lap);
+            fp_lap_vec<D, M, T, false>(st, col, j, k, h0, lap);  // FP64 adds: the integer path costs registers here
             ldv<T, VEC>(FL + v * VEC, rv);
 #pragma unroll
             for (int x = 0; x < VEC; ++x) out[x] = fma(ih2, lap[x], rv[x]);
