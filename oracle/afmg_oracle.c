@@ -60,6 +60,7 @@ typedef struct {
 
 typedef struct {
     int D, N, max_level;
+    int nr[3];                      /* root boxes per axis (the domain is nr[0] x nr[1] x nr[2]) */
     int nbox;
     OBox *box;
     int L;                          /* highest level present */
@@ -86,6 +87,9 @@ static int pwrap(const OTree *t, int a, int q, int side) {
 }
 
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
+
+/* boxes per axis a at a level: nr[a] root boxes, each split 2^(level-1) times */
+static int side_of(const OTree *t, int a, int level) { return t->nr[a] << (level - 1); }
 
 static uint64_t morton_key(int D, const int *idx) {
     uint64_t k = 0;
@@ -124,9 +128,8 @@ static int cmp_pos(const void *pa, const void *pb) {
 /* binary search for (level, idx) in the canonical order; -1 when absent */
 static int find_box(const OTree *t, int level, const int *idx) {
     if (level < 1 || level > t->L) return -1;
-    int side = 1 << (level - 1);
     for (int a = 0; a < t->D; a++)
-        if (idx[a] < 1 || idx[a] > side) return -1;
+        if (idx[a] < 1 || idx[a] > side_of(t, a, level)) return -1;
     uint64_t key = morton_key(t->D, idx);
     int lo = t->lstart[level], hi = lo + t->lcount[level] - 1;
     while (lo <= hi) {
@@ -169,12 +172,12 @@ static int rebuild(OTree *t, OPos *pos, int n) {
             for (int a = 0; a < t->D; a++) q[a] = 2 * b->idx[a] - 1 + ((c >> a) & 1);
             b->child[c] = find_box(t, b->level + 1, q);
         }
-        int side = 1 << (b->level - 1);
         for (int d = 0; d < ONDIR; d++) b->nb[d] = -1;
         for (int d = 0; d < nd; d++) {
             int off[3], q[3] = {1, 1, 1}, outside = 0;
             dir_offsets(t->D, d, off);
             for (int a = 0; a < t->D; a++) {
+                int side = side_of(t, a, b->level);
                 q[a] = pwrap(t, a, b->idx[a] + off[a], side);
                 if (q[a] < 1 || q[a] > side) outside = 1;
             }
@@ -190,15 +193,44 @@ static int rebuild(OTree *t, OPos *pos, int n) {
     return 0;
 }
 
-OTree *ot_create(int D, int N, int max_level) {
+/* the tree made of its root boxes alone (level 1), nr[0] x nr[1] (x nr[2]) */
+static int rebuild_roots(OTree *t) {
+    int R = t->nr[0] * t->nr[1] * t->nr[2];
+    OPos *pos = malloc(sizeof(OPos) * (size_t)R);
+    if (!pos) return -3;
+    for (int r = 0; r < R; r++) {
+        pos[r].level = 1;
+        pos[r].idx[0] = r % t->nr[0] + 1;
+        pos[r].idx[1] = (r / t->nr[0]) % t->nr[1] + 1;
+        pos[r].idx[2] = r / (t->nr[0] * t->nr[1]) + 1;
+        pos[r].key = morton_key(t->D, pos[r].idx);
+    }
+    int rc = rebuild(t, pos, R);
+    free(pos);
+    return rc;
+}
+
+/* A tree whose coarsest level is a rectangular block of root boxes, each the
+ * unit square/cube (Sec. 2.2: a domain of several root boxes; the boxes
+ * below them form several coarse boxes per level, Sec. 3.2). */
+OTree *ot_create_roots(int D, int N, int max_level, const int *nroot) {
     if (D < 2 || D > 3 || N < 4 || N % 2 || N > 64 || max_level < 1) return NULL;
     if (max_level > (D == 3 ? 21 : OMAXLEV)) return NULL;
+    for (int a = 0; a < 3; a++) {
+        int r = a < D ? nroot[a] : 1;
+        if (r < 1 || r > 64) return NULL;
+        if (((long long)r << (max_level - 1)) > (1LL << 21)) return NULL;  /* Morton keys: 21 bits per axis */
+    }
     OTree *t = calloc(1, sizeof(OTree));
     t->D = D; t->N = N; t->max_level = max_level;
-    OPos root = {1, 0, {1, 1, 1}};
-    root.key = morton_key(D, root.idx);
-    rebuild(t, &root, 1);
+    for (int a = 0; a < 3; a++) t->nr[a] = a < D ? nroot[a] : 1;
+    rebuild_roots(t);
     return t;
+}
+
+OTree *ot_create(int D, int N, int max_level) {
+    const int one[3] = {1, 1, 1};
+    return ot_create_roots(D, N, max_level, one);
 }
 
 void ot_destroy(OTree *t) {
@@ -300,7 +332,7 @@ void ot_face_centers(const OTree *t, double *xyz) {
             tang_axes(D, s, &t1, &t2);
             for (int f = 0; f < nf; f++) {
                 double x[3];
-                x[a] = (s % 2) ? 1.0 : 0.0;
+                x[a] = (s % 2) ? (double)t->nr[a] : 0.0;
                 x[t1] = ((b->idx[t1] - 1) * N + f % N + 0.5) * h;
                 if (t2 >= 0) x[t2] = ((b->idx[t2] - 1) * N + f / N + 0.5) * h;
                 for (int c = 0; c < D; c++) xyz[o * D + c] = x[c];
@@ -355,7 +387,7 @@ int ot_adapt(OTree *t, const signed char *flags, int nbuf, int *n_added, int *n_
                 if (t->box[b].nb[d] != -1) continue;
                 int off[3], q[3] = {1, 1, 1};
                 dir_offsets(D, d, off);
-                for (int a = 0; a < D; a++) q[a] = (pwrap(t, a, t->box[b].idx[a] + off[a], 1 << (l - 1)) + 1) / 2;
+                for (int a = 0; a < D; a++) q[a] = (pwrap(t, a, t->box[b].idx[a] + off[a], side_of(t, a, l)) + 1) / 2;
                 int c = find_box(t, l - 1, q);
                 if (c < 0 || !isleaf[c]) { free(ref); free(rm); free(isleaf); free(leafpos); return -4; }
                 ref[c] = 1;
@@ -434,52 +466,60 @@ int ot_mg_setup(OTree *t) {
     int D = t->D, N = t->N;
     int nsub = 0;
     for (int M = N / 2; M >= 2; M /= 2) nsub++;
+    /* R root boxes (the level-1 boxes, canonical order); below each of them
+     * one box per coarse level, connected like the roots */
+    const int R = t->lcount[1], r0 = t->lstart[1];
+    const int nsubR = nsub * R;
     t->lmin = 1 - nsub;
-    t->nmg = nsub + t->nbox;
+    t->nmg = nsubR + t->nbox;
     t->mg = calloc((size_t)t->nmg, sizeof(OMG));
     for (int i = 0; i < 2 * OMAXLEV + 8; i++) { t->mgstart[i] = 0; t->mgcount[i] = 0; }
-    /* boxes below the root: level lmin .. 0, one each */
+    /* boxes below the roots: level lmin .. 0, R each, in the roots' order */
     for (int i = 0; i < nsub; i++) {
-        OMG *m = &t->mg[i];
-        m->level = t->lmin + i;
-        m->M = N >> (1 - m->level);
-        m->h = 1.0 / m->M;
-        m->tbox = -1;
-        m->parent = i > 0 ? i - 1 : -1;
-        m->refined = 1;
-        for (int s = 0; s < 2 * D; s++) {
-            /* one box per level: across a periodic side it is its own neighbour */
-            if (t->bct[s] == 2) { m->kind[s] = K_SAME; m->nbid[s] = i; }
-            else { m->kind[s] = K_PHYS; m->nbid[s] = -1; }
+        for (int r = 0; r < R; r++) {
+            OMG *m = &t->mg[i * R + r];
+            m->level = t->lmin + i;
+            m->M = N >> (1 - m->level);
+            m->h = 1.0 / m->M;
+            m->tbox = -1;
+            m->parent = i > 0 ? (i - 1) * R + r : -1;
+            m->refined = 1;
+            for (int s = 0; s < 2 * D; s++) {
+                /* the root's neighbour across side s (itself across a periodic
+                 * side of a one-root axis) */
+                int q = t->box[r0 + r].nb[side_dir(D, s)];
+                if (q >= 0) { m->kind[s] = K_SAME; m->nbid[s] = i * R + (q - r0); }
+                else { m->kind[s] = K_PHYS; m->nbid[s] = -1; }
+            }
         }
-        t->mgstart[m->level - t->lmin] = i; t->mgcount[m->level - t->lmin] = 1;
+        t->mgstart[i] = i * R; t->mgcount[i] = R;
     }
     for (int b = 0; b < t->nbox; b++) {
-        OMG *m = &t->mg[nsub + b];
+        OMG *m = &t->mg[nsubR + b];
         const OBox *tb = &t->box[b];
         m->level = tb->level; m->M = N; m->h = cell_h(t, tb->level);
         m->tbox = b;
         m->refined = tb->child[0] >= 0;
         if (tb->level == 1) {
-            m->parent = nsub > 0 ? nsub - 1 : -1;
+            m->parent = nsub > 0 ? (nsub - 1) * R + (b - r0) : -1;
             for (int a = 0; a < 3; a++) m->poff[a] = 0;
         } else {
-            m->parent = nsub + tb->parent;
+            m->parent = nsubR + tb->parent;
             for (int a = 0; a < D; a++) m->poff[a] = ((tb->idx[a] - 1) & 1) * (N / 2);
         }
         for (int s = 0; s < 2 * D; s++) {
             int q = tb->nb[side_dir(D, s)];
-            if (q >= 0) { m->kind[s] = K_SAME; m->nbid[s] = nsub + q; }
+            if (q >= 0) { m->kind[s] = K_SAME; m->nbid[s] = nsubR + q; }
             else if (q == -2) { m->kind[s] = K_PHYS; m->nbid[s] = -1; }
             else {
                 /* refinement boundary: the coarse box is the parent's neighbour */
                 int cq = t->box[tb->parent].nb[side_dir(D, s)];
                 if (cq < 0) return -4;
-                m->kind[s] = K_CF; m->nbid[s] = nsub + cq;
+                m->kind[s] = K_CF; m->nbid[s] = nsubR + cq;
             }
         }
         int li = tb->level - t->lmin;
-        if (t->mgcount[li] == 0) t->mgstart[li] = nsub + b;
+        if (t->mgcount[li] == 0) t->mgstart[li] = nsubR + b;
         t->mgcount[li]++;
     }
     for (int i = 0; i < t->nmg; i++) {
@@ -910,7 +950,7 @@ void ot_set_homogeneous(OTree *t, int hom) { t->hom = hom; }
  * centre, and the ghost g = u_1 + h b makes the face flux (g - u_1)/h equal
  * to b.  Periodic (Sec. 2.2: the neighbour beyond the last box is the first)
  * applies to both sides of an axis; it changes the connectivity, so it can
- * only be switched on or off while the tree is the root box alone.  A tree
+ * only be switched on or off while the tree is its root boxes alone.  A tree
  * with no Dirichlet side is singular and is refused. */
 int ot_set_bc_types(OTree *t, const int *types) {
     int any_dirichlet = 0, change = 0;
@@ -921,13 +961,9 @@ int ot_set_bc_types(OTree *t, const int *types) {
         change |= (types[s] == 2) != (t->bct[s] == 2);
     }
     if (!any_dirichlet) return -1;
-    if (change && t->nbox != 1) return -1;
+    if (change && t->nbox != t->nr[0] * t->nr[1] * t->nr[2]) return -1;
     for (int s = 0; s < 2 * t->D; s++) t->bct[s] = types[s];
-    if (change) {
-        OPos root = {1, 0, {1, 1, 1}};
-        root.key = morton_key(t->D, root.idx);
-        return rebuild(t, &root, 1);
-    }
+    if (change) return rebuild_roots(t);
     return 0;
 }
 

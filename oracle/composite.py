@@ -23,11 +23,12 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def assemble(dim, box_n, level, idx, children, bc_types=None):
+def assemble(dim, box_n, level, idx, children, bc_types=None, roots=None):
     """level/idx/children: canonical box arrays (export format); bc_types: per
     domain side (-x,+x,-y,+y[,-z,+z]) 0 = Dirichlet, 1 = Neumann, 2 = periodic
-    (default all 0)."""
+    (default all 0); roots: root boxes per axis (default one)."""
     D, N = dim, box_n
+    nr = list(roots) if roots is not None else [1] * D
     bct = list(bc_types) if bc_types is not None else [0] * (2 * D)
     periodic = [bct[2 * a] == 2 for a in range(D)]
     nbox = len(level)
@@ -55,14 +56,14 @@ def assemble(dim, box_n, level, idx, children, bc_types=None):
         l = int(level[b])
         h = 1.0 / (N * 2 ** (l - 1))
         ih2 = 1.0 / (h * h)
-        ncoarse = N * 2 ** (l - 1)  # cells per axis at this level
+        ncells = [nr[a] * N * 2 ** (l - 1) for a in range(D)]  # cells per axis at this level
         # boundary faces of this box, in side order
         face_base = {}
         for s in range(2 * D):
             a, hi = s // 2, s % 2
             if periodic[a]:
                 continue
-            if (hi == 0 and idx[b][a] == 1) or (hi == 1 and idx[b][a] == 2 ** (l - 1)):
+            if (hi == 0 and idx[b][a] == 1) or (hi == 1 and idx[b][a] == nr[a] * 2 ** (l - 1)):
                 face_base[s] = nface
                 nface += N ** (D - 1)
         base = (idx[b] - 1) * N
@@ -75,8 +76,8 @@ def assemble(dim, box_n, level, idx, children, bc_types=None):
                 q = g.copy()
                 q[a] += sgn
                 if periodic[a]:
-                    q[a] %= ncoarse
-                if q[a] < 0 or q[a] >= ncoarse:
+                    q[a] %= ncells[a]
+                if q[a] < 0 or q[a] >= ncells[a]:
                     neumann = bct[s] == 1
                     rows.append(me); cols.append(me); vals.append(ih2 if neumann else -ih2)
                     tang = [t for t in range(D) if t != a]
@@ -117,9 +118,10 @@ def cell_volumes(dim, box_n, level, children):
     return np.repeat(h ** dim, box_n ** dim)
 
 
-def face_areas(dim, box_n, level, idx, children, bc_types=None):
+def face_areas(dim, box_n, level, idx, children, bc_types=None, roots=None):
     """h^(D-1) for each boundary face, canonical face order."""
     bct = list(bc_types) if bc_types is not None else [0] * (2 * dim)
+    nr = list(roots) if roots is not None else [1] * dim
     out = []
     for b in np.nonzero(children[:, 0] < 0)[0]:
         l = int(level[b])
@@ -128,6 +130,6 @@ def face_areas(dim, box_n, level, idx, children, bc_types=None):
             a, hi = s // 2, s % 2
             if bct[2 * a] == 2:
                 continue
-            if (hi == 0 and idx[b][a] == 1) or (hi == 1 and idx[b][a] == 2 ** (l - 1)):
+            if (hi == 0 and idx[b][a] == 1) or (hi == 1 and idx[b][a] == nr[a] * 2 ** (l - 1)):
                 out.extend([h ** (dim - 1)] * box_n ** (dim - 1))
     return np.array(out)

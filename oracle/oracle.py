@@ -46,7 +46,7 @@ def lib():
         L = ctypes.CDLL(LIB)
         P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
         sig = {
-            "ot_create": (P, [I, I, I]), "ot_destroy": (None, [P]),
+            "ot_create": (P, [I, I, I]), "ot_create_roots": (P, [I, I, I, P]), "ot_destroy": (None, [P]),
             "ot_refine_uniform": (I, [P, I]), "ot_nbox": (I, [P]), "ot_nleaf": (I, [P]),
             "ot_highest_level": (I, [P]), "ot_nleaf_cells": (LL, [P]),
             "ot_export": (None, [P, P, P, P, P, P]), "ot_cell_centers": (None, [P, P]),
@@ -77,12 +77,18 @@ def _p(a):
 
 
 class OracleTree:
-    """One quadtree (D=2) or octree (D=3) on [0,1]^D with a single root box of
-    N^D cells (Sec. 2.1-2.2), plus the FP64 multigrid data on it."""
+    """One quadtree (D=2) or octree (D=3) with root boxes of N^D cells
+    (Sec. 2.1-2.2), plus the FP64 multigrid data on it.  By default a single
+    root box on [0,1]^D; roots=(rx, ry[, rz]) makes the domain a block of
+    rx x ry (x rz) unit root boxes, [0,rx] x [0,ry] (x [0,rz])."""
 
-    def __init__(self, dim, box_n, max_level):
+    def __init__(self, dim, box_n, max_level, roots=None):
         self.D, self.N, self.max_level = dim, box_n, max_level
-        self._h = lib().ot_create(dim, box_n, max_level)
+        self.roots = tuple(int(r) for r in roots) if roots is not None else (1,) * dim
+        if len(self.roots) != dim:
+            raise ValueError("roots needs one count per axis")
+        nr = np.array(list(self.roots) + [1] * (3 - dim), np.int32)
+        self._h = lib().ot_create_roots(dim, box_n, max_level, _p(nr))
         if not self._h:
             raise ValueError("bad tree parameters")
         self._mg = False
@@ -188,11 +194,11 @@ class OracleTree:
 
     def set_boundary_types(self, types):
         """Per domain side (-x,+x,-y,+y[,-z,+z]): 0 Dirichlet, 1 Neumann, 2 periodic
-        (both sides of an axis; switched only while the tree is the root box)."""
+        (both sides of an axis; switched only while the tree is its root boxes alone)."""
         t = np.ascontiguousarray(types, dtype=np.int32)
         assert t.size == 2 * self.D
         if lib().ot_set_bc_types(self._h, _p(t)) != 0:
-            raise ValueError("boundary types: 0/1/2, periodic in pairs and set on the root box alone, "
+            raise ValueError("boundary types: 0/1/2, periodic in pairs and set on the root boxes alone, "
                              "at least one Dirichlet side")
         self.bc_types = [int(v) for v in t]
 

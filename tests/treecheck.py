@@ -23,8 +23,10 @@ def directions(D):
     return out
 
 
-def check_tree(e, D, N=None, periodic=()):
-    """periodic: axes whose neighbours wrap around (Sec. 2.2)."""
+def check_tree(e, D, N=None, periodic=(), roots=None):
+    """periodic: axes whose neighbours wrap around (Sec. 2.2); roots: root
+    boxes per axis (default one)."""
+    nr = list(roots) if roots is not None else [1] * D
     level, idx, parent, children, nbs = e["level"], e["idx"], e["parent"], e["children"], e["neighbours"]
     n = len(level)
     pos = {(int(level[b]),) + tuple(int(v) for v in idx[b]): b for b in range(n)}
@@ -34,7 +36,7 @@ def check_tree(e, D, N=None, periodic=()):
     dirs = directions(D)
     for b in range(n):
         l = int(level[b])
-        side = 2 ** (l - 1)
+        side = [nr[a] * 2 ** (l - 1) for a in range(D)]
         # parent / children from spatial indices
         if l == 1:
             assert parent[b] == -1
@@ -46,8 +48,8 @@ def check_tree(e, D, N=None, periodic=()):
         assert all(k >= 0 for k in kids) or all(k < 0 for k in kids)  # never partially refined
         for d, off in enumerate(dirs):
             q = [int(idx[b][a]) + off[a] for a in range(D)]
-            q = [(v - 1) % side + 1 if a in periodic else v for a, v in enumerate(q)]
-            if any(v < 1 or v > side for v in q):
+            q = [(v - 1) % side[a] + 1 if a in periodic else v for a, v in enumerate(q)]
+            if any(v < 1 or v > side[a] for a, v in enumerate(q)):
                 assert nbs[b, d] == -2
             else:
                 want = pos.get((l,) + tuple(q), -1)
@@ -63,8 +65,9 @@ def check_tree(e, D, N=None, periodic=()):
     shifts = [s for s in itertools.product((-1, 0, 1), repeat=D) if all(s[a] == 0 or a in periodic for a in range(D))]
     for i in range(len(leaves)):
         for sh in shifts:  # periodic images touch across the wrapped sides
-            lo_i, hi_i = lo[i] + np.array(sh), hi[i] + np.array(sh)
+            shift = np.array(sh) * np.array(nr)
+            lo_i, hi_i = lo[i] + shift, hi[i] + shift
             touch = np.all((lo <= hi_i + 1e-12) & (hi >= lo_i - 1e-12), axis=1)
             assert np.all(np.abs(lv[touch] - lv[i]) <= 1), "2:1 balance violated"
     # leaves tile the domain
-    assert abs(sum(1.0 / 2.0 ** (D * (level[b] - 1)) for b in leaves) - 1.0) < 1e-12
+    assert abs(sum(1.0 / 2.0 ** (D * (level[b] - 1)) for b in leaves) - float(np.prod(nr))) < 1e-12
