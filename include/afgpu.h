@@ -96,6 +96,17 @@ const char *afg_last_error(void);
 /* Create a tree on [0,1]^dim with one root box of box_n^dim cells (level 1).
  * dim in {2,3}; box_n in {4,8,16}; 1 <= max_level <= 21 (3D) or 30 (2D). */
 int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out);
+
+/* Create a tree whose level 1 is a block of root boxes (Sec. 2.2: the coarse
+ * grid of a non-square domain holds several boxes): nroot (host memory, dim
+ * ints, each in [1, 64]) root boxes per axis, each the unit square/cube, so
+ * the domain is [0,nroot[0]] x [0,nroot[1]] (x [0,nroot[2]]).  Root boxes
+ * come first in the canonical box order (Morton order of their indices).
+ * The tree calls (refine, adapt, boundary types, export, centres) accept such
+ * trees; the multigrid calls (set_rhs onwards) return AFG_ERR_STATE for them
+ * when nroot is not all ones.  Also AFG_ERR_ARG when nroot[a] << (max_level-1)
+ * exceeds 2^21. */
+int afg_tree_create_roots(int dim, int box_n, int max_level, const int *nroot, afg_tree **out);
 int afg_tree_destroy(afg_tree *t);
 
 /* CUDA stream (cudaStream_t) for all device work of this tree; NULL = default. */

@@ -53,7 +53,8 @@ _LIB = None
 P, I, LL, DBL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
 _SIGS = {
     "afg_default_opts": (None, [P]), "afg_last_error": (ctypes.c_char_p, []),
-    "afg_tree_create": (I, [I, I, I, P]), "afg_tree_destroy": (I, [P]), "afg_set_stream": (I, [P, P]),
+    "afg_tree_create": (I, [I, I, I, P]), "afg_tree_create_roots": (I, [I, I, I, P, P]),
+    "afg_tree_destroy": (I, [P]), "afg_set_stream": (I, [P, P]),
     "afg_refine_uniform": (I, [P, I]), "afg_cell_centers": (I, [P, P]), "afg_face_centers": (I, [P, P]),
     "afg_leaf_levels": (I, [P, P]), "afg_adapt": (I, [P, P, I, P, P]), "afg_info": (I, [P, P]),
     "afg_export_tree": (I, [P, P, P, P, P, P]), "afg_set_rhs": (I, [P, P]), "afg_set_dirichlet": (I, [P, P]),
@@ -138,12 +139,22 @@ def _stream_ptr():
 
 class Tree:
     """A quadtree (dim=2) or octree (dim=3) on [0,1]^dim, root box of box_n^dim
-    cells (Sec. 2.1-2.2), with its multigrid data on the GPU."""
+    cells (Sec. 2.1-2.2), with its multigrid data on the GPU.  roots=(rx, ry[,
+    rz]) makes level 1 a block of root boxes, the domain [0,rx] x [0,ry] (x
+    [0,rz]); such trees support the tree calls, not yet the multigrid calls."""
 
-    def __init__(self, dim, box_n, max_level):
+    def __init__(self, dim, box_n, max_level, roots=None):
         self.D, self.N, self.max_level = dim, box_n, max_level
         h = ctypes.c_void_p()
-        _check(lib().afg_tree_create(dim, box_n, max_level, ctypes.byref(h)))
+        if roots is None:
+            self.roots = (1,) * dim
+            _check(lib().afg_tree_create(dim, box_n, max_level, ctypes.byref(h)))
+        else:
+            self.roots = tuple(int(r) for r in roots)
+            if len(self.roots) != dim:
+                raise ValueError("roots needs one count per axis")
+            nr = (ctypes.c_int * dim)(*self.roots)
+            _check(lib().afg_tree_create_roots(dim, box_n, max_level, nr, ctypes.byref(h)))
         self._h = h
 
     def close(self):

@@ -361,6 +361,22 @@ int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out) {
     AFG_API_END
 }
 
+int afg_tree_create_roots(int dim, int box_n, int max_level, const int *nroot, afg_tree **out) {
+    if (!out || !nroot) return fail(AFG_ERR_ARG, "null argument");
+    if (dim != 2 && dim != 3) return fail(AFG_ERR_ARG, "dim must be 2 or 3");
+    if (box_n != 4 && box_n != 8 && box_n != 16) return fail(AFG_ERR_ARG, "box_n must be 4, 8 or 16");
+    if (max_level < 1 || max_level > (dim == 3 ? 21 : 30)) return fail(AFG_ERR_ARG, "max_level out of range");
+    for (int a = 0; a < dim; ++a) {
+        if (nroot[a] < 1 || nroot[a] > 64) return fail(AFG_ERR_ARG, "root boxes per axis must be in [1, 64]");
+        if (((long long)nroot[a] << (max_level - 1)) > (1LL << 21))
+            return fail(AFG_ERR_ARG, "boxes per axis on max_level exceed 2^21 (Morton keys)");
+    }
+    AFG_API_BEGIN
+    *out = new afg_tree(dim, box_n, max_level, nroot);
+    return AFG_OK;
+    AFG_API_END
+}
+
 int afg_tree_destroy(afg_tree *t) {
     delete t;
     return AFG_OK;
@@ -412,7 +428,7 @@ int afg_face_centers(const afg_tree *t, double *xyz) {
                 if (e != a) ta[k++] = e;
             for (int f = 0; f < nf; ++f, ++o) {
                 double x[3];
-                x[a] = (s & 1) ? 1.0 : 0.0;
+                x[a] = (s & 1) ? (double)h.nr[a] : 0.0;
                 x[ta[0]] = ((bx.idx[ta[0]] - 1) * N + f % N + 0.5) * hh;
                 if (D == 3) x[ta[1]] = ((bx.idx[ta[1]] - 1) * N + f / N + 0.5) * hh;
                 for (int e = 0; e < D; ++e) xyz[o * D + e] = x[e];

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <stdexcept>
 
 #include "grid.h"
 
@@ -36,6 +37,13 @@ T *upload(const std::vector<T> &v, std::vector<std::unique_ptr<DevBuf>> &owned) 
 }  // namespace
 
 Grid::Grid(const std::vector<const HostTree *> &trees) {
+    // the device hierarchy below level 1 holds one box per tree (the root's
+    // coarse grids, solved in one block); a block of several root boxes needs
+    // coarse levels of several connected boxes, which the device path lacks
+    for (const HostTree *h : trees)
+        if (h->nroots() != 1)
+            throw std::runtime_error("multigrid on a tree of several root boxes is not available on the GPU; "
+                                     "the tree calls (refine, adapt, export, centres) are");
     D = trees[0]->D;
     N = trees[0]->N;
     T = (int)trees.size();

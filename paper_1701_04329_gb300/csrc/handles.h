@@ -13,7 +13,7 @@ struct afg_tree {
     std::unique_ptr<afg::Grid> grid;
     int grid_version = -1;
     cudaStream_t stream = nullptr;
-    afg_tree(int d, int n, int m) : ht(d, n, m) {}
+    afg_tree(int d, int n, int m, const int *nroot = nullptr) : ht(d, n, m, nroot) {}
 };
 
 struct afg_forest {

@@ -22,11 +22,20 @@ uint64_t morton_key(int D, const int idx[3]) {
     return k;
 }
 
-HostTree::HostTree(int dim, int box_n, int maxl) : D(dim), N(box_n), max_level(maxl) {
-    HBox root{};
-    root.level = 1;
-    root.idx[0] = root.idx[1] = root.idx[2] = 1;
-    std::vector<HBox> pos{root};
+HostTree::HostTree(int dim, int box_n, int maxl, const int *nroot) : D(dim), N(box_n), max_level(maxl) {
+    if (nroot)
+        for (int a = 0; a < D; ++a) nr[a] = nroot[a];
+    std::vector<HBox> pos;
+    for (int k = 1; k <= nr[2]; ++k)
+        for (int j = 1; j <= nr[1]; ++j)
+            for (int i = 1; i <= nr[0]; ++i) {
+                HBox root{};
+                root.level = 1;
+                root.idx[0] = i;
+                root.idx[1] = j;
+                root.idx[2] = k;
+                pos.push_back(root);
+            }
     rebuild(std::move(pos));
 }
 
@@ -57,9 +66,8 @@ int HostTree::side_dir(int s) const {
 
 int HostTree::find(int level, const int idx[3]) const {
     if (level < 1 || level > L) return -1;
-    const int side = 1 << (level - 1);
     for (int a = 0; a < D; ++a)
-        if (idx[a] < 1 || idx[a] > side) return -1;
+        if (idx[a] < 1 || idx[a] > side_of(a, level)) return -1;
     const auto &m = lookup_[level];
     auto it = m.find(morton_key(D, idx));
     return it == m.end() ? -1 : it->second;
@@ -86,7 +94,7 @@ int HostTree::set_boundary_types(const int *types, std::string &err) {
         change |= (types[s] == 2) != (bct[s] == 2);
     }
     if (!any_dirichlet) { err = "at least one side must be Dirichlet (the problem is singular otherwise)"; return -1; }
-    if (change && boxes.size() != 1) { err = "periodic sides can only be switched while the tree is the root box"; return -1; }
+    if (change && (int)boxes.size() != nroots()) { err = "periodic sides can only be switched while the tree is its root boxes"; return -1; }
     bool same = true;
     for (int s = 0; s < 2 * D; ++s) same &= bct[s] == types[s];
     if (same) return 0;
@@ -126,13 +134,13 @@ void HostTree::rebuild(std::vector<HBox> &&pos) {
             for (int a = 0; a < D; ++a) q[a] = 2 * b.idx[a] - 1 + ((c >> a) & 1);
             b.child[c] = find(b.level + 1, q);
         }
-        const int side = 1 << (b.level - 1);
         for (int d = 0; d < 26; ++d) b.nb[d] = -1;
         for (int d = 0; d < nd; ++d) {
             int off[3], q[3] = {1, 1, 1};
             dir_offset(d, off);
             bool inside = true;
             for (int a = 0; a < D; ++a) {
+                const int side = side_of(a, b.level);
                 q[a] = wrap(a, b.idx[a] + off[a], side);
                 inside = inside && q[a] >= 1 && q[a] <= side;
             }
@@ -229,7 +237,7 @@ int HostTree::adapt(const int8_t *flags, int n_buf, int *n_added, int *n_removed
                 if (boxes[b].nb[d] != -1) continue;
                 int off[3], q[3] = {1, 1, 1};
                 dir_offset(d, off);
-                for (int a = 0; a < D; ++a) q[a] = (wrap(a, boxes[b].idx[a] + off[a], 1 << (l - 1)) + 1) >> 1;
+                for (int a = 0; a < D; ++a) q[a] = (wrap(a, boxes[b].idx[a] + off[a], side_of(a, l)) + 1) >> 1;
                 const int c = find(l - 1, q);
                 if (c < 0 || !boxes[c].leaf()) { err = "adapt: tree not 2:1 balanced"; return -4; }
                 refine[c] = 1;

@@ -23,9 +23,12 @@ struct HBox {
 
 class HostTree {
   public:
-    HostTree(int dim, int box_n, int max_level);
+    // nroot: root boxes per axis (null = one); the domain is the block of
+    // nroot[0] x nroot[1] (x nroot[2]) unit root boxes (Sec. 2.2)
+    HostTree(int dim, int box_n, int max_level, const int *nroot = nullptr);
 
     int D, N, max_level;
+    int nr[3] = {1, 1, 1};             // root boxes per axis
     std::vector<HBox> boxes;           // canonical order
     std::vector<int> lstart, lcount;   // per level (index = level)
     int L = 0;                         // highest level present
@@ -37,6 +40,8 @@ class HostTree {
     int bct[6] = {0, 0, 0, 0, 0, 0};   // per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann, 2 periodic
 
     int ndir() const;                  // 3^D - 1
+    int nroots() const { return nr[0] * nr[1] * nr[2]; }
+    int side_of(int a, int level) const { return nr[a] << (level - 1); }  // boxes per axis
     int side_dir(int s) const;         // face side (-x,+x,-y,...) -> direction index
     void dir_offset(int d, int off[3]) const;
     int find(int level, const int idx[3]) const;  // box id or -1
@@ -44,7 +49,7 @@ class HostTree {
 
     int refine_uniform(int level, std::string &err);
     // side types; periodicity (both sides of an axis) changes the connectivity and is
-    // accepted only while the tree is the root box alone
+    // accepted only while the tree is its root boxes alone
     int set_boundary_types(const int *types, std::string &err);
     int wrap(int a, int q, int side) const;  // index q on axis a, wrapped on a periodic axis
     int adapt(const int8_t *flags, int n_buf, int *n_added, int *n_removed, std::string &err);

@@ -75,3 +75,30 @@ def test_periodic_adapt_sequences(D, N, seed, types):
         assert a.adapt(flags, nbuf) == b.adapt(flags, nbuf)
         check_tree(same_tree(a, b), D, periodic=periodic)
     assert len(a.face_centers()) == b.n_bfaces
+
+
+@pytest.mark.parametrize("D,N,roots,types,seed", [(2, 4, (2, 1), None, 41), (2, 8, (3, 2), [2, 2, 0, 1], 42),
+                                                  (2, 4, (1, 3), [0, 0, 2, 2], 43), (3, 4, (2, 1, 1), None, 44),
+                                                  (3, 4, (1, 2, 2), [0, 1, 2, 2, 0, 0], 45)])
+def test_multiroot_adapt_sequences(D, N, roots, types, seed):
+    """Level 1 a block of root boxes (Sec. 2.2): both builders agree bit for
+    bit (root order, neighbours across root boundaries, 2:1 refinement across
+    them and across wrapped sides), as do cell and face centres."""
+    rng = np.random.default_rng(seed)
+    maxl = 5 if D == 2 else 4
+    a, b = OracleTree(D, N, maxl, roots=roots), afgpu.Tree(D, N, maxl, roots=roots)
+    for t in (a, b):
+        if types is not None:
+            t.set_boundary_types(types)
+        t.refine_uniform(2)
+    periodic = tuple(x for x in range(D) if types is not None and types[2 * x] == 2)
+    check_tree(same_tree(a, b), D, roots=roots, periodic=periodic)
+    for step in range(5):
+        n = a.n_leaf_cells
+        assert n == b.n_leaf_cells
+        flags = rng.choice(np.array([-1, 0, 1], np.int8), size=n, p=[0.4, 0.5, 0.1])
+        flags[np.repeat(rng.random(n // N ** D) < 0.4, N ** D)] = -1
+        nbuf = int(rng.integers(0, 3))
+        assert a.adapt(flags, nbuf) == b.adapt(flags, nbuf)
+        check_tree(same_tree(a, b), D, roots=roots, periodic=periodic)
+    assert len(a.face_centers()) == b.n_bfaces
