@@ -54,7 +54,9 @@ typedef struct {
     int poff[3];        /* offset (cells) of this box's region inside the parent */
     int refined;        /* 1 if finer boxes exist below it (values are FAS values) */
     int kind[6], nbid[6];
+    double x0[3];       /* lower corner of the box */
     double *u, *rho, *vold, *r, *rr, *d;
+    double *eps;        /* coefficient of the variable-coefficient operators, ghosts included */
     double *bc[6];
 } OMG;
 
@@ -76,6 +78,7 @@ typedef struct {
     int mgstart[2 * OMAXLEV + 8], mgcount[2 * OMAXLEV + 8]; /* indexed by level - lmin */
     int hom;                         /* 1: homogeneous boundary data (defect equations) */
     int bct[6];                      /* per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann, 2 periodic */
+    int op;                          /* 0 Laplacian, 1 div(eps grad), 2 the same in (r,z) with r = x (2D) */
 } OTree;
 
 /* spatial index q along axis a at a level with `side` boxes per axis: on a
@@ -450,7 +453,7 @@ static void free_mg(OTree *t) {
     if (!t->mg) { t->mg_ready = 0; return; }
     for (int i = 0; i < t->nmg; i++) {
         OMG *m = &t->mg[i];
-        free(m->u); free(m->rho); free(m->vold); free(m->r); free(m->rr); free(m->d);
+        free(m->u); free(m->rho); free(m->vold); free(m->r); free(m->rr); free(m->d); free(m->eps);
         for (int s = 0; s < 6; s++) free(m->bc[s]);
     }
     free(t->mg);
@@ -484,6 +487,7 @@ int ot_mg_setup(OTree *t) {
             m->tbox = -1;
             m->parent = i > 0 ? (i - 1) * R + r : -1;
             m->refined = 1;
+            for (int a = 0; a < 3; a++) m->x0[a] = a < D ? (double)(t->box[r0 + r].idx[a] - 1) : 0.0;
             for (int s = 0; s < 2 * D; s++) {
                 /* the root's neighbour across side s (itself across a periodic
                  * side of a one-root axis) */
@@ -499,6 +503,7 @@ int ot_mg_setup(OTree *t) {
         const OBox *tb = &t->box[b];
         m->level = tb->level; m->M = N; m->h = cell_h(t, tb->level);
         m->tbox = b;
+        for (int a = 0; a < 3; a++) m->x0[a] = a < D ? (double)(tb->idx[a] - 1) * N * m->h : 0.0;
         m->refined = tb->child[0] >= 0;
         if (tb->level == 1) {
             m->parent = nsub > 0 ? (nsub - 1) * R + (b - r0) : -1;
@@ -528,7 +533,9 @@ int ot_mg_setup(OTree *t) {
         m->u = calloc(ng, sizeof(double)); m->rho = calloc(ng, sizeof(double));
         m->vold = calloc(ng, sizeof(double)); m->r = calloc(ng, sizeof(double));
         m->rr = calloc(ng, sizeof(double)); m->d = calloc(ng, sizeof(double));
-        if (!m->u || !m->rho || !m->vold || !m->r || !m->rr || !m->d) return -3;
+        m->eps = malloc(ng * sizeof(double));
+        if (!m->u || !m->rho || !m->vold || !m->r || !m->rr || !m->d || !m->eps) return -3;
+        for (size_t g = 0; g < ng; g++) m->eps[g] = 1.0;
         for (int s = 0; s < 2 * D; s++)
             if (m->kind[s] == K_PHYS) m->bc[s] = calloc((size_t)ipow(m->M, D - 1), sizeof(double));
     }
@@ -649,7 +656,7 @@ static void fill_ghosts(OTree *t, int level, int which) {
     for (int i = i0; i < i1; i++) {
         OMG *m = &t->mg[i];
         int M = m->M;
-        double *v = which == 0 ? m->u : m->d;
+        double *v = which == 0 ? m->u : which == 1 ? m->d : m->eps;
         for (int s = 0; s < 2 * D; s++) {
             int a = s / 2, t1, t2;
             tang_axes(D, s, &t1, &t2);
@@ -668,21 +675,27 @@ static void fill_ghosts(OTree *t, int level, int which) {
                 int ii = GI(M, p1[0], p1[1], p1[2]);
                 if (m->kind[s] == K_SAME) {
                     OMG *q = &t->mg[m->nbid[s]];
-                    double *w = which == 0 ? q->u : q->d;
+                    double *w = which == 0 ? q->u : which == 1 ? q->d : q->eps;
                     int pq[3]; memcpy(pq, pg, sizeof pg);
                     pq[a] = (s % 2 == 0) ? M : 1;
                     v[gi] = w[GI(M, pq[0], pq[1], pq[2])];
+                } else if (m->kind[s] == K_PHYS && which == 2) {
+                    v[gi] = v[ii];  /* the coefficient is mirrored: the face takes the cell's own */
                 } else if (m->kind[s] == K_PHYS) {
                     double bval = (which == 0 && !t->hom) ? m->bc[s][f] : 0.0;
                     if (t->bct[s] == 1) v[gi] = v[ii] + m->h * bval;
                     else v[gi] = 2.0 * bval - v[ii];
-                } else if (which == 0) {
-                    /* coarse-fine; only the solution u ever needs this */
+                } else if (which != 1) {
+                    /* coarse-fine; the correction d never needs this */
                     OMG *q = &t->mg[m->nbid[s]];
                     int pc[3] = {0, 0, 0};
                     pc[a] = (s % 2 == 0) ? q->M : 1;
                     pc[t1] = m->poff[t1] + c1 / 2 + 1;
                     if (t2 >= 0) pc[t2] = m->poff[t2] + c2 / 2 + 1;
+                    if (which == 2) {  /* the coefficient of the coarse cell across the face */
+                        v[gi] = q->eps[GI(q->M, pc[0], pc[1], pc[2])];
+                        continue;
+                    }
                     double uH = q->u[GI(q->M, pc[0], pc[1], pc[2])];
                     int pt[3]; memcpy(pt, p1, sizeof pt);
                     pt[t1] = (c1 % 2 == 0) ? c1 + 2 : c1; /* partner: 1-based c1+1 odd -> +1 */
@@ -709,6 +722,8 @@ static double nbsum(int D, int M, const double *v, int i, int j, int k) {
     return s;
 }
 
+static void wsum(const OTree *t, const OMG *m, const double *v, int i, int j, int k, double *sv, double *sc);
+
 /* One half-sweep of red-black Gauss-Seidel (Sec. 3.1) on all boxes of a
  * level.  Colour 0 (red) = cells whose 1-based indices sum to an even number.
  * For the Poisson operator the local solve is u = (sum nb - h^2 rho)/(2D). */
@@ -726,7 +741,13 @@ static void gsrb_half(OTree *t, int level, int colour) {
                 for (int i = 1; i <= M; i++) {
                     if ((i + j + k) % 2 != colour) continue;
                     int g = GI(M, i, j, k);
-                    m->u[g] = (nbsum(D, M, m->u, i, j, k) - h2 * m->rho[g]) * inv;
+                    if (t->op) {  /* local solve of the variable-coefficient equation */
+                        double sv, sc;
+                        wsum(t, m, m->u, i, j, k, &sv, &sc);
+                        m->u[g] = (sv - h2 * m->rho[g]) / sc;
+                    } else {
+                        m->u[g] = (nbsum(D, M, m->u, i, j, k) - h2 * m->rho[g]) * inv;
+                    }
                 }
     }
 }
@@ -747,6 +768,52 @@ static double lap(int D, int M, double h, const double *v, int i, int j, int k) 
     return (nbsum(D, M, v, i, j, k) - 2.0 * D * v[GI(M, i, j, k)]) / (h * h);
 }
 
+/* Variable-coefficient operators (Sec. 3.4-3.5), div(eps grad u) = rho:
+ * the flux through the face between cells of coefficients e1 and e2 is the
+ * harmonic mean 2 e1 e2 / (e1 + e2) times the difference quotient (Sec. 3.4:
+ * the local reconstruction with a jump of eps at the face).  In (r,z)
+ * coordinates (2D, r = x) the divergence is (1/r) d/dr (r eps du/dr) +
+ * d/dz (eps du/dz), so the r-faces are also weighted by r_face / r_cell, and
+ * the face on the axis r = 0 carries no flux.  c[s] is the coefficient of
+ * side s (-x,+x,-y,+y,-z,+z) of cell (i,j,k) of box m (ghosts of eps filled). */
+static void face_coef(const OTree *t, const OMG *m, int i, int j, int k, double *c) {
+    const int D = t->D, M = m->M;
+    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+    const double e0 = m->eps[GI(M, i, j, k)];
+    for (int s = 0; s < 2 * D; s++) {
+        const double en = m->eps[GI(M, nb[s][0], nb[s][1], nb[s][2])];
+        c[s] = 2.0 * e0 * en / (e0 + en);
+    }
+    if (t->op == 2) {
+        const double rc = m->x0[0] + (i - 0.5) * m->h;
+        c[0] *= (m->x0[0] + (i - 1) * m->h) / rc;
+        c[1] *= (m->x0[0] + i * m->h) / rc;
+    }
+}
+
+/* sum_s c_s v_s and sum_s c_s over the faces of cell (i,j,k), in side order */
+static void wsum(const OTree *t, const OMG *m, const double *v, int i, int j, int k, double *sv, double *sc) {
+    const int D = t->D, M = m->M;
+    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+    double c[6], a = 0.0, b = 0.0;
+    face_coef(t, m, i, j, k, c);
+    for (int s = 0; s < 2 * D; s++) {
+        a += c[s] * v[GI(M, nb[s][0], nb[s][1], nb[s][2])];
+        b += c[s];
+    }
+    *sv = a;
+    *sc = b;
+}
+
+/* A_h(v) at one cell for the tree's operator (needs filled ghosts):
+ * (sum_s c_s (v_s - v)) / h^2 */
+static double op_apply(const OTree *t, const OMG *m, const double *v, int i, int j, int k) {
+    if (t->op == 0) return lap(t->D, m->M, m->h, v, i, j, k);
+    double sv, sc;
+    wsum(t, m, v, i, j, k, &sv, &sc);
+    return (sv - sc * v[GI(m->M, i, j, k)]) / (m->h * m->h);
+}
+
 /* residual r = rho - A_h(u) (Eq. residual) on all boxes of a level */
 static void residual_level(OTree *t, int level) {
     int D = t->D, li = level - t->lmin;
@@ -759,14 +826,14 @@ static void residual_level(OTree *t, int level) {
             for (int j = 1; j <= M; j++)
                 for (int i = 1; i <= M; i++) {
                     int g = GI(M, i, j, k);
-                    m->r[g] = m->rho[g] - lap(D, M, m->h, m->u, i, j, k);
+                    m->r[g] = m->rho[g] - op_apply(t, m, m->u, i, j, k);
                 }
     }
 }
 
 /* Restriction by averaging the 2^D children (Sec. 2.5): every box of `level`
  * writes the mean of its cells into its region of the parent.  which: 0 = u
- * into u, 1 = r into rr. */
+ * into u, 1 = r into rr, 2 = eps into eps. */
 static void restrict_level(OTree *t, int level, int which) {
     int D = t->D, li = level - t->lmin;
     int i0 = t->mgstart[li], i1 = i0 + t->mgcount[li];
@@ -774,19 +841,32 @@ static void restrict_level(OTree *t, int level, int which) {
     for (int b = i0; b < i1; b++) {
         OMG *m = &t->mg[b];
         OMG *p = &t->mg[m->parent];
-        const double *src = which == 0 ? m->u : m->r;
-        double *dst = which == 0 ? p->u : p->rr;
+        const double *src = which == 0 ? m->u : which == 1 ? m->r : m->eps;
+        double *dst = which == 0 ? p->u : which == 1 ? p->rr : p->eps;
         int Mh = m->M / 2;
         for (int K = 0; K < (D == 3 ? Mh : 1); K++)
             for (int J = 0; J < Mh; J++)
                 for (int I = 0; I < Mh; I++) {
+                    int pk = D == 3 ? m->poff[2] + K + 1 : 0;
+                    double *out = &dst[GI(p->M, m->poff[0] + I + 1, m->poff[1] + J + 1, pk)];
+                    if (t->op == 2) {
+                        /* (r,z): the mean weighted by the children's volumes, proportional to r */
+                        double s = 0.0, w = 0.0;
+                        for (int dy = 0; dy < 2; dy++)
+                            for (int dx = 0; dx < 2; dx++) {
+                                const double r = m->x0[0] + (2 * I + dx + 0.5) * m->h;
+                                s += r * src[GI(m->M, 2 * I + 1 + dx, 2 * J + 1 + dy, 0)];
+                                w += r;
+                            }
+                        *out = s / w;
+                        continue;
+                    }
                     double s = 0.0;
                     for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
                         for (int dy = 0; dy < 2; dy++)
                             for (int dx = 0; dx < 2; dx++)
                                 s += src[GI(m->M, 2 * I + 1 + dx, 2 * J + 1 + dy, D == 3 ? 2 * K + 1 + dz : 0)];
-                    int pk = D == 3 ? m->poff[2] + K + 1 : 0;
-                    dst[GI(p->M, m->poff[0] + I + 1, m->poff[1] + J + 1, pk)] = s / (double)(1 << D);
+                    *out = s / (double)(1 << D);
                 }
     }
 }
@@ -807,7 +887,7 @@ static void fas_coarse(OTree *t, int level) {
             for (int j = 1; j <= M; j++)
                 for (int i = 1; i <= M; i++) {
                     int g = GI(M, i, j, k);
-                    m->rho[g] = m->rr[g] + lap(D, M, m->h, m->u, i, j, k);
+                    m->rho[g] = m->rr[g] + op_apply(t, m, m->u, i, j, k);
                 }
     }
 }
@@ -917,7 +997,7 @@ void ot_residual_norm(OTree *t, double *rmax, double *rhomax) {
             for (int j = 1; j <= M; j++)
                 for (int i = 1; i <= M; i++) {
                     int g = GI(M, i, j, k);
-                    double r = fabs(m->rho[g] - lap(D, M, m->h, m->u, i, j, k));
+                    double r = fabs(m->rho[g] - op_apply(t, m, m->u, i, j, k));
                     if (r > rm) rm = r;
                     if (fabs(m->rho[g]) > pm) pm = fabs(m->rho[g]);
                 }
@@ -937,12 +1017,47 @@ void ot_apply_A(OTree *t, const double *u, double *out) {
         OMG *m = leaf_mg(t, li);
         for (int c = 0; c < nc; c++) {
             int M = m->M, i = c % M + 1, j = (c / M) % M + 1, k = D == 3 ? c / (M * M) + 1 : 0;
-            out[(long long)li * nc + c] = lap(D, M, m->h, m->u, i, j, k);
+            out[(long long)li * nc + c] = op_apply(t, m, m->u, i, j, k);
         }
     }
 }
 
 void ot_set_homogeneous(OTree *t, int hom) { t->hom = hom; }
+
+/* Operator of the tree (Sec. 3.5): 0 the Laplacian, 1 div(eps grad u) with
+ * harmonic-mean face coefficients, 2 the same in (r,z) coordinates (2D only;
+ * r = x, the -x side of the domain is the axis r = 0).  Reading: eps is given
+ * per leaf cell (ot_set_eps, after ot_set_operator); coarse cells take the
+ * mean of their children (the restriction of Sec. 2.5; in (r,z) every
+ * restriction is the mean weighted by the children's volumes, r at their
+ * centres -- with the plain mean the (r,z) cycles stall), which keeps the
+ * value when, as Sec. 3.4 requires, eps jumps only at faces of the coarsest
+ * cells; ghost values are
+ * copied from the same-level neighbour, taken from the coarse cell across a
+ * refinement boundary, and mirrored at the domain boundary (a boundary face
+ * takes its cell's coefficient).  Neumann data stays the normal derivative
+ * of u, so the boundary flux is eps b. */
+int ot_set_operator(OTree *t, int op) {
+    if (op < 0 || op > 2 || (op == 2 && t->D != 2)) return -1;
+    t->op = op;
+    return 0;
+}
+
+int ot_set_eps(OTree *t, const double *eps) {
+    if (!t->mg_ready) return -1;
+    int D = t->D, nc = ipow(t->N, D);
+    for (int li = 0; li < t->nleaf; li++) {
+        OMG *m = leaf_mg(t, li);
+        for (int c = 0; c < nc; c++) {
+            double e = eps[(long long)li * nc + c];
+            if (!(e > 0.0)) return -1;
+            m->eps[interior_index(D, m->M, c)] = e;
+        }
+    }
+    for (int l = t->L; l > t->lmin; l--) restrict_level(t, l, 2);
+    for (int l = t->lmin; l <= t->L; l++) fill_ghosts(t, l, 2);
+    return 0;
+}
 
 /* Boundary type of each domain side (Sec. 2 lists Dirichlet, Neumann and
  * periodic conditions, given through ghost cells; Sec. 3 allows a mix).
@@ -983,6 +1098,7 @@ static long long leaf_cell_id(OTree *t, int *leafpos, int mgb, int i, int j, int
 }
 
 long long ot_leaf_rows(OTree *t, int *row, int *col, double *val) {
+    if (t->op != 0) return -1;  /* the rows restate the Laplacian's ghost rules only */
     int D = t->D, N = t->N, nc = ipow(N, D), nsub = t->nmg - t->nbox;
     int *leafpos = malloc(sizeof(int) * (size_t)t->nbox);
     for (int i = 0; i < t->nbox; i++) leafpos[i] = -1;

@@ -62,7 +62,7 @@ def lib():
             "ot_mg_set": (None, [P, I, I, P]), "ot_fill_ghosts": (None, [P, I, I]),
             "ot_smooth": (None, [P, I, I]), "ot_gsrb_half": (None, [P, I, I]),
             "ot_restrict": (None, [P, I, I]), "ot_correct": (None, [P, I]),
-            "ot_set_bc_types": (I, [P, P]),
+            "ot_set_bc_types": (I, [P, P]), "ot_set_operator": (I, [P, I]), "ot_set_eps": (I, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -201,6 +201,22 @@ class OracleTree:
             raise ValueError("boundary types: 0/1/2, periodic in pairs and set on the root boxes alone, "
                              "at least one Dirichlet side")
         self.bc_types = [int(v) for v in t]
+
+    def set_operator(self, op):
+        """0: Laplacian; 1: div(eps grad u) with harmonic-mean face
+        coefficients (Sec. 3.4); 2: the same in (r,z) coordinates, r = x (2D)."""
+        if lib().ot_set_operator(self._h, int(op)) != 0:
+            raise ValueError("operator: 0, 1, or 2 (2D only)")
+        self.op = int(op)
+
+    def set_eps(self, eps):
+        """Coefficient per leaf cell (> 0), canonical order; coarse levels take
+        the mean of their children.  Set again after every change of the tree."""
+        self._need_mg()
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        assert eps.size == self.n_leaf_cells
+        if lib().ot_set_eps(self._h, _p(eps)) != 0:
+            raise ValueError("eps must be positive")
 
     def set_homogeneous(self, hom):
         self._need_mg()
