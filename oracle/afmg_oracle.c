@@ -54,6 +54,7 @@ typedef struct {
     int poff[3];        /* offset (cells) of this box's region inside the parent */
     int refined;        /* 1 if finer boxes exist below it (values are FAS values) */
     int kind[6], nbid[6];
+    int nball[26];      /* same-level neighbour (multigrid id) in every direction, -1 none */
     double x0[3];       /* lower corner of the box */
     double *u, *rho, *vold, *r, *rr, *d;
     double *eps;        /* coefficient of the variable-coefficient operators, ghosts included */
@@ -79,6 +80,7 @@ typedef struct {
     int hom;                         /* 1: homogeneous boundary data (defect equations) */
     int bct[6];                      /* per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann, 2 periodic */
     int op;                          /* 0 Laplacian, 1 div(eps grad), 2 the same in (r,z) with r = x (2D) */
+    int prolong;                     /* correction: 0 linear 2-1-1 / 1-1-1-1, 1 bi/trilinear, 2 zeroth order */
 } OTree;
 
 /* spatial index q along axis a at a level with `side` boxes per axis: on a
@@ -495,6 +497,10 @@ int ot_mg_setup(OTree *t) {
                 if (q >= 0) { m->kind[s] = K_SAME; m->nbid[s] = i * R + (q - r0); }
                 else { m->kind[s] = K_PHYS; m->nbid[s] = -1; }
             }
+            for (int d = 0; d < ONDIR; d++) {
+                int q = d < ipow(3, D) - 1 ? t->box[r0 + r].nb[d] : -1;
+                m->nball[d] = q >= 0 ? i * R + (q - r0) : -1;
+            }
         }
         t->mgstart[i] = i * R; t->mgcount[i] = R;
     }
@@ -511,6 +517,10 @@ int ot_mg_setup(OTree *t) {
         } else {
             m->parent = nsubR + tb->parent;
             for (int a = 0; a < D; a++) m->poff[a] = ((tb->idx[a] - 1) & 1) * (N / 2);
+        }
+        for (int d = 0; d < ONDIR; d++) {
+            int q = d < ipow(3, D) - 1 ? tb->nb[d] : -1;
+            m->nball[d] = q >= 0 ? nsubR + q : -1;
         }
         for (int s = 0; s < 2 * D; s++) {
             int q = tb->nb[side_dir(D, s)];
@@ -715,6 +725,63 @@ static void fill_ghosts(OTree *t, int level, int which) {
     }
 }
 
+/* Edge and corner ghost cells (Sec. 2.4) of variable `which` (0 = u, 1 = d)
+ * of all boxes of a level, after the side ghosts: copied from the diagonal
+ * neighbour when it exists at the same level, otherwise linearly
+ * extrapolated -- in 2D the corner ghost gets b + c - a (b, c the two side
+ * ghosts next to it, a the corner cell); in 3D an edge ghost likewise from
+ * its two side ghosts and the edge cell, and a corner ghost from the edge
+ * ghost next to it along x, the side ghost next to it along y-z and the
+ * corner cell: f(p) = f(p + u) + f(p + w) - f(p + u + w) for the unit steps
+ * u (into the box along the first ghost axis) and w (along the others), which
+ * is exact for linear f.  Edges are filled before corners. */
+static void fill_corner_ghosts(OTree *t, int level, int which) {
+    int D = t->D, li = level - t->lmin, nd = ipow(3, D) - 1;
+    int i0 = t->mgstart[li], i1 = i0 + t->mgcount[li];
+    for (int pass = 2; pass <= D; pass++) {
+#pragma omp parallel for schedule(static)
+        for (int b = i0; b < i1; b++) {
+            OMG *m = &t->mg[b];
+            int M = m->M;
+            double *v = which == 0 ? m->u : m->d;
+            for (int d = 0; d < nd; d++) {
+                int off[3];
+                dir_offsets(D, d, off);
+                int nz = 0, ax[3], na = 0;
+                for (int a = 0; a < D; a++) if (off[a]) { nz++; ax[na++] = a; }
+                if (nz != pass) continue;
+                const OMG *q = m->nball[d] >= 0 ? &t->mg[m->nball[d]] : NULL;
+                const double *w = q ? (which == 0 ? q->u : q->d) : NULL;
+                int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+                for (int a = 0; a < D; a++) {
+                    if (off[a] < 0) lo[a] = hi[a] = 0;
+                    else if (off[a] > 0) lo[a] = hi[a] = M + 1;
+                    else { lo[a] = 1; hi[a] = M; }
+                }
+                for (int k = lo[2]; k <= hi[2]; k++)
+                    for (int j = lo[1]; j <= hi[1]; j++)
+                        for (int i = lo[0]; i <= hi[0]; i++) {
+                            int p[3] = {i, j, k};
+                            if (w) {
+                                int pq[3] = {i, j, k};
+                                for (int a = 0; a < D; a++)
+                                    if (off[a] < 0) pq[a] = M; else if (off[a] > 0) pq[a] = 1;
+                                v[GI(M, p[0], p[1], p[2])] = w[GI(M, pq[0], pq[1], pq[2])];
+                                continue;
+                            }
+                            int pu[3] = {i, j, k}, pw[3] = {i, j, k}, pa[3] = {i, j, k};
+                            /* u: step in along the first ghost axis; w: along the others */
+                            pu[ax[0]] = off[ax[0]] < 0 ? 1 : M;
+                            for (int e = 1; e < na; e++) pw[ax[e]] = off[ax[e]] < 0 ? 1 : M;
+                            for (int e = 0; e < na; e++) pa[ax[e]] = off[ax[e]] < 0 ? 1 : M;
+                            v[GI(M, p[0], p[1], p[2])] = v[GI(M, pu[0], pu[1], pu[2])] + v[GI(M, pw[0], pw[1], pw[2])]
+                                                         - v[GI(M, pa[0], pa[1], pa[2])];
+                        }
+            }
+        }
+    }
+}
+
 /* sum of the 2D face neighbours of cell g, order ((x-+x+)+(y-+y+))+(z-+z+) */
 static double nbsum(int D, int M, const double *v, int i, int j, int k) {
     double s = (v[GI(M, i - 1, j, k)] + v[GI(M, i + 1, j, k)]) + (v[GI(M, i, j - 1, k)] + v[GI(M, i, j + 1, k)]);
@@ -907,6 +974,7 @@ static void correct_level(OTree *t, int level) {
         for (int g = 0; g < ng; g++) m->d[g] = m->u[g] - m->vold[g];
     }
     fill_ghosts(t, level - 1, 1);
+    if (t->prolong == 1) fill_corner_ghosts(t, level - 1, 1);
     int li = level - t->lmin;
     int i0 = t->mgstart[li], i1 = i0 + t->mgcount[li];
 #pragma omp parallel for schedule(static)
@@ -923,6 +991,26 @@ static void correct_level(OTree *t, int level) {
                         sgn[a] = (f[a] % 2 == 1) ? -1 : 1;
                     }
                     double d0 = p->d[GI(p->M, C[0], C[1], C[2])];
+                    if (t->prolong == 2) {  /* zeroth order: the coarse value */
+                        m->u[GI(M, i, j, k)] += d0;
+                        continue;
+                    }
+                    if (t->prolong == 1) {
+                        /* bi/trilinear: the 2^D nearest coarse cells, weight 3/4 per
+                         * axis for the nearer one and 1/4 for the farther one */
+                        double add = 0.0;
+                        for (int c = 0; c < (1 << D); c++) {
+                            int q[3] = {C[0], C[1], C[2]};
+                            double wgt = 1.0;
+                            for (int a = 0; a < D; a++) {
+                                if ((c >> a) & 1) { q[a] += sgn[a]; wgt *= 0.25; }
+                                else wgt *= 0.75;
+                            }
+                            add += wgt * p->d[GI(p->M, q[0], q[1], q[2])];
+                        }
+                        m->u[GI(M, i, j, k)] += add;
+                        continue;
+                    }
                     double dx = p->d[GI(p->M, C[0] + sgn[0], C[1], C[2])];
                     double dy = p->d[GI(p->M, C[0], C[1] + sgn[1], C[2])];
                     double add;
@@ -1023,6 +1111,17 @@ void ot_apply_A(OTree *t, const double *u, double *out) {
 }
 
 void ot_set_homogeneous(OTree *t, int hom) { t->hom = hom; }
+
+/* Prolongation of the coarse-grid correction (Sec. 2.5 lists these schemes;
+ * Sec. 4.1 notes that a higher order one lowers the convergence factor):
+ * 0 linear with weights (1/2,1/4,1/4) / (1/4,1/4,1/4,1/4) (the default),
+ * 1 bilinear / trilinear (it reads edge and corner ghosts of the coarse
+ * difference), 2 zeroth order (the coarse value). */
+int ot_set_prolong(OTree *t, int scheme) {
+    if (scheme < 0 || scheme > 2) return -1;
+    t->prolong = scheme;
+    return 0;
+}
 
 /* Operator of the tree (Sec. 3.5): 0 the Laplacian, 1 div(eps grad u) with
  * harmonic-mean face coefficients, 2 the same in (r,z) coordinates (2D only;
@@ -1187,6 +1286,7 @@ void ot_mg_set(OTree *t, int b, int var, const double *in) {
     memcpy(v, in, sizeof(double) * (size_t)ncells_g(t->D, m->M));
 }
 void ot_fill_ghosts(OTree *t, int level, int which) { fill_ghosts(t, level, which); }
+void ot_fill_corner_ghosts(OTree *t, int level, int which) { fill_corner_ghosts(t, level, which); }
 void ot_smooth(OTree *t, int level, int n) { smooth(t, level, n); }
 void ot_gsrb_half(OTree *t, int level, int colour) { gsrb_half(t, level, colour); }
 void ot_restrict(OTree *t, int level, int which) { restrict_level(t, level, which); }

@@ -63,6 +63,7 @@ def lib():
             "ot_smooth": (None, [P, I, I]), "ot_gsrb_half": (None, [P, I, I]),
             "ot_restrict": (None, [P, I, I]), "ot_correct": (None, [P, I]),
             "ot_set_bc_types": (I, [P, P]), "ot_set_operator": (I, [P, I]), "ot_set_eps": (I, [P, P]),
+            "ot_set_prolong": (I, [P, I]), "ot_fill_corner_ghosts": (None, [P, I, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -217,6 +218,15 @@ class OracleTree:
         assert eps.size == self.n_leaf_cells
         if lib().ot_set_eps(self._h, _p(eps)) != 0:
             raise ValueError("eps must be positive")
+
+    def set_prolong(self, scheme):
+        """Prolongation of the coarse-grid correction: 0 linear (1/2,1/4,1/4)
+        / (1/4,...) (default), 1 bilinear / trilinear, 2 zeroth order."""
+        if lib().ot_set_prolong(self._h, int(scheme)) != 0:
+            raise ValueError("prolongation: 0, 1 or 2")
+
+    def fill_corner_ghosts(self, level, which=0):
+        lib().ot_fill_corner_ghosts(self._h, level, which)
 
     def set_homogeneous(self, hom):
         self._need_mg()
