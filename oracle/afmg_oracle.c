@@ -1112,6 +1112,110 @@ void ot_apply_A(OTree *t, const double *u, double *out) {
 
 void ot_set_homogeneous(OTree *t, int hom) { t->hom = hom; }
 
+/* value at fine cell f (1-based, in a child box at offset poff of its
+ * parent) prolonged from the parent's ghosted array p (M cells per side):
+ * scheme 0 linear (1/2,1/4,1/4) / (1/4,1/4,1/4,1/4), 1 bi/trilinear, 2 copy */
+static double prolong_value(int D, int M, const double *p, const int *poff, const int *f, int scheme) {
+    int C[3] = {0, 0, 0}, sgn[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) {
+        C[a] = poff[a] + (f[a] + 1) / 2;
+        sgn[a] = (f[a] % 2 == 1) ? -1 : 1;
+    }
+    double d0 = p[GI(M, C[0], C[1], C[2])];
+    if (scheme == 2) return d0;
+    if (scheme == 1) {
+        double add = 0.0;
+        for (int c = 0; c < (1 << D); c++) {
+            int q[3] = {C[0], C[1], C[2]};
+            double w = 1.0;
+            for (int a = 0; a < D; a++) {
+                if ((c >> a) & 1) { q[a] += sgn[a]; w *= 0.25; }
+                else w *= 0.75;
+            }
+            add += w * p[GI(M, q[0], q[1], q[2])];
+        }
+        return add;
+    }
+    double dx = p[GI(M, C[0] + sgn[0], C[1], C[2])];
+    double dy = p[GI(M, C[0], C[1] + sgn[1], C[2])];
+    if (D == 2) return 0.5 * d0 + 0.25 * (dx + dy);
+    double dz = p[GI(M, C[0], C[1], C[2] + sgn[2])];
+    return 0.25 * (((d0 + dx) + dy) + dz);
+}
+
+/* Mesh adaptation with a leaf field carried along (Sec. 2.3: with
+ * prolongation and restriction routines given, they are applied when the
+ * mesh changes): u_old on the current leaves (canonical order) becomes u_new
+ * on the adapted leaves.  A leaf that stays keeps its values; a parent whose
+ * children are removed gets their mean (the restriction of Sec. 2.5); the
+ * children of a refined leaf are prolonged from it with `scheme` (as
+ * ot_set_prolong), its ghosts filled as in the solver (same-level copy, the
+ * stored boundary data, the refinement-boundary scheme, and for the
+ * bi/trilinear scheme the edge/corner ghosts).  The stored solution is
+ * overwritten; the multigrid data is rebuilt afterwards. */
+int ot_adapt_transfer(OTree *t, const signed char *flags, int nbuf, int scheme, const double *u_old,
+                      double *u_new, int *n_added, int *n_removed) {
+    if (scheme < 0 || scheme > 2) return -1;
+    int D = t->D, N = t->N, nc = ipow(N, D), ng = ncells_g(D, N);
+    if (!t->mg_ready && ot_mg_setup(t) != 0) return -3;
+    ot_set_solution(t, u_old);
+    for (int l = t->L; l > 1; l--) restrict_level(t, l, 0);
+    for (int l = 1; l <= t->L; l++) {
+        fill_ghosts(t, l, 0);
+        if (scheme == 1) fill_corner_ghosts(t, l, 0);
+    }
+    int nold = t->nbox, nsub = t->nmg - t->nbox;
+    int *olev = malloc(sizeof(int) * (size_t)nold);
+    uint64_t *okey = malloc(sizeof(uint64_t) * (size_t)nold);
+    double *odata = malloc(sizeof(double) * (size_t)nold * (size_t)ng);
+    if (!olev || !okey || !odata) { free(olev); free(okey); free(odata); return -3; }
+    for (int b = 0; b < nold; b++) {
+        olev[b] = t->box[b].level;
+        okey[b] = t->box[b].key;
+        memcpy(odata + (size_t)b * ng, t->mg[nsub + b].u, sizeof(double) * (size_t)ng);
+    }
+    int rc = ot_adapt(t, flags, nbuf, n_added, n_removed);
+    if (rc) { free(olev); free(okey); free(odata); return rc; }
+    /* old boxes are in canonical order: binary search on (level, key) */
+    for (int li = 0; li < t->nleaf; li++) {
+        const OBox *nb = &t->box[t->leaf[li]];
+        int found = -1, lo = 0, hi = nold - 1;
+        while (lo <= hi) {
+            int mid = (lo + hi) / 2;
+            if (olev[mid] == nb->level && okey[mid] == nb->key) { found = mid; break; }
+            if (olev[mid] < nb->level || (olev[mid] == nb->level && okey[mid] < nb->key)) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        double *out = u_new + (long long)li * nc;
+        if (found >= 0) {  /* a leaf that stays, or a parent that became a leaf (restricted values) */
+            for (int c = 0; c < nc; c++) out[c] = odata[(size_t)found * ng + interior_index(D, N, c)];
+            continue;
+        }
+        /* a new child of a refined leaf */
+        int pidx[3] = {1, 1, 1}, poff[3] = {0, 0, 0};
+        for (int a = 0; a < D; a++) {
+            pidx[a] = (nb->idx[a] + 1) / 2;
+            poff[a] = ((nb->idx[a] - 1) & 1) * (N / 2);
+        }
+        uint64_t pkey = morton_key(D, pidx);
+        int par = -1;
+        lo = 0; hi = nold - 1;
+        while (lo <= hi) {
+            int mid = (lo + hi) / 2;
+            if (olev[mid] == nb->level - 1 && okey[mid] == pkey) { par = mid; break; }
+            if (olev[mid] < nb->level - 1 || (olev[mid] == nb->level - 1 && okey[mid] < pkey)) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        if (par < 0) { free(olev); free(okey); free(odata); return -4; }
+        for (int c = 0; c < nc; c++) {
+            int f[3] = {c % N + 1, (c / N) % N + 1, D == 3 ? c / (N * N) + 1 : 0};
+            out[c] = prolong_value(D, N, odata + (size_t)par * ng, poff, f, scheme);
+        }
+    }
+    free(olev); free(okey); free(odata);
+    return 0;
+}
+
 /* Prolongation of the coarse-grid correction (Sec. 2.5 lists these schemes;
  * Sec. 4.1 notes that a higher order one lowers the convergence factor):
  * 0 linear with weights (1/2,1/4,1/4) / (1/4,1/4,1/4,1/4) (the default),

@@ -64,6 +64,7 @@ def lib():
             "ot_restrict": (None, [P, I, I]), "ot_correct": (None, [P, I]),
             "ot_set_bc_types": (I, [P, P]), "ot_set_operator": (I, [P, I]), "ot_set_eps": (I, [P, P]),
             "ot_set_prolong": (I, [P, I]), "ot_fill_corner_ghosts": (None, [P, I, I]),
+            "ot_adapt_transfer": (I, [P, P, I, I, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -159,6 +160,25 @@ class OracleTree:
             raise RuntimeError("adapt failed (%d)" % rc)
         self._mg = False
         return a.value, r.value
+
+    def adapt_transfer(self, flags, u, n_buf=2, scheme=0):
+        """adapt() that carries the leaf field u along: kept leaves copy,
+        derefined parents average their children, new children are prolonged
+        (scheme 0 linear, 1 bi/trilinear, 2 copy).  Returns (u_new, added,
+        removed); the stored solution is overwritten."""
+        self._need_mg()
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert flags.size == self.n_leaf_cells and u.size == self.n_leaf_cells
+        # the adapted tree has at most 2^D times the leaves
+        out = np.zeros(self.n_leaf_cells * 2 ** self.D)
+        a, r = ctypes.c_int(0), ctypes.c_int(0)
+        rc = lib().ot_adapt_transfer(self._h, _p(flags), n_buf, scheme, _p(u), _p(out), ctypes.byref(a),
+                                     ctypes.byref(r))
+        if rc != 0:
+            raise RuntimeError("adapt_transfer failed (%d)" % rc)
+        self._mg = False
+        return out[:self.n_leaf_cells].copy(), a.value, r.value
 
     # ---- multigrid data ----------------------------------------------------
     def _need_mg(self):
