@@ -220,12 +220,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def dist_init():
+def dist_init(backend=None):
+    """One process per GPU (torchrun env); NCCL on GPUs, gloo without them
+    (the CPU tests of the multi-rank timing)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend or ("nccl" if torch.cuda.is_available() else "gloo"))
         return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
 
@@ -236,10 +239,12 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, x):
+    """The slowest rank's time: every rank gets the maximum."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
