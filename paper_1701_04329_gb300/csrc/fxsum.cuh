@@ -32,6 +32,11 @@
 #else
 #define AFG_HD inline
 #endif
+#ifdef __CUDA_ARCH__
+#define AFG_FX_UNROLL _Pragma("unroll")
+#else
+#define AFG_FX_UNROLL
+#endif
 
 namespace afg {
 
@@ -119,14 +124,14 @@ struct FxAcc {
 template <int K, int C = 0>
 AFG_HD bool fx_sum(const double *x, double c, double &out) {
     int E = C ? fx_exp(c) : 0;
-#pragma unroll
+AFG_FX_UNROLL
     for (int k = 0; k < K; ++k) {
         const int e = fx_exp(x[k]);
         E = e > E ? e : E;
     }
     FxAcc<K + C> acc(E);
     if (!acc.ok()) return false;
-#pragma unroll
+AFG_FX_UNROLL
     for (int k = 0; k < K; ++k) acc.add(x[k]);
     if (C) acc.add(c, -C);
     out = acc.round();
