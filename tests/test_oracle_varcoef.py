@@ -242,3 +242,26 @@ def test_paper_jump_layout_converges(op):
     f = [hist[i + 1] / hist[i] for i in range(len(hist) - 1)]
     mean = (hist[-1] / hist[0]) ** (1.0 / (len(hist) - 1))
     assert hist[-1] <= 1e-11 and mean <= 0.2 and max(f) <= 0.35, f
+
+
+@pytest.mark.parametrize("D,op", [(2, 1), (3, 1), (2, 2)])
+def test_uniform_operator_is_symmetric(D, op):
+    """On a uniform tree with Dirichlet sides the face coefficient is shared
+    by the two cells, so the operator is symmetric: K in Cartesian
+    coordinates, diag(r) K in (r,z) (the finite-volume weights).  Assembled
+    from the box machinery (A applied to unit vectors)."""
+    t = OracleTree(D, 4, 2)
+    t.refine_uniform(2)
+    t.set_operator(op)
+    rng = np.random.default_rng(17 + D + op)
+    t.set_eps(np.exp(rng.normal(size=t.n_leaf_cells)))
+    t.set_dirichlet(np.zeros(t.n_bfaces))
+    n = t.n_leaf_cells
+    K = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        K[:, j] = t.apply_A(e)
+    W = np.diag(t.cell_centers()[:, 0]) if op == 2 else np.eye(n)
+    S = W @ K
+    assert np.abs(S - S.T).max() <= 1e-12 * np.abs(S).max()
