@@ -11,8 +11,11 @@ true transpose is needed.  Two solvers:
 * direct(): scipy sparse LU of K^T (the definition, for small trees);
 * bicgstab(): BiCGStab (van der Vorst 1992) with right preconditioner
   W M W^-1, M = one oracle V-cycle from zero with homogeneous boundary data,
-  W = diag(cell volumes) -- W K is symmetric up to the refinement-boundary
-  terms, so W M W^-1 approximates K^-T.
+  W = diag(cell volumes, times r in (r,z)) -- W K is symmetric up to the
+  refinement-boundary terms, so W M W^-1 approximates K^-T.
+
+With a variable coefficient (Sec. 3.4-3.5) the face terms carry the face
+coefficients, and dL/db_f takes them too (-B^T lam with B of that operator).
 """
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -20,23 +23,44 @@ import scipy.sparse.linalg as spla
 from . import composite
 
 
+def operator(tree):
+    """(K, B) of the tree's composite system: the Laplacian's rows from the
+    oracle's ghost rules, or the geometric assembly of a variable-coefficient
+    operator (Sec. 3.4-3.5) with the coefficient last set on the tree."""
+    e = tree.export()
+    bct = getattr(tree, "bc_types", None)
+    roots = getattr(tree, "roots", None)
+    op = getattr(tree, "op", 0)
+    if op == 0:
+        _, B = composite.assemble(tree.D, tree.N, e["level"], e["idx"], e["children"], bct, roots=roots)
+        return tree.leaf_rows(), B
+    return composite.assemble_var(tree.D, tree.N, e["level"], e["idx"], e["children"], tree.eps, op, bct,
+                                  roots=roots)
+
+
+def weights(tree):
+    """Cell volumes; in (r,z) times r (the finite-volume weights)."""
+    e = tree.export()
+    w = composite.cell_volumes(tree.D, tree.N, e["level"], e["children"])
+    if getattr(tree, "op", 0) == 2:
+        w = w * tree.cell_centers()[:, 0]
+    return w
+
+
 def direct(tree, g):
-    K = tree.leaf_rows()
+    K, _ = operator(tree)
     return spla.spsolve(K.T.tocsc(), g)
 
 
 def dl_db(tree, lam):
-    e = tree.export()
-    _, B = composite.assemble(tree.D, tree.N, e["level"], e["idx"], e["children"],
-                              getattr(tree, "bc_types", None))
+    _, B = operator(tree)
     return -(B.T @ lam)
 
 
 def bicgstab(tree, g, tol=1e-12, maxit=100, n_down=2, n_up=2, n_base=4):
     """The tree's rhs/solution/boundary data are overwritten."""
-    KT = tree.leaf_rows().T.tocsr()
-    e = tree.export()
-    w = composite.cell_volumes(tree.D, tree.N, e["level"], e["children"])
+    KT = operator(tree)[0].T.tocsr()
+    w = weights(tree)
     tree.set_dirichlet(np.zeros(tree.n_bfaces))
     tree.set_homogeneous(1)
 

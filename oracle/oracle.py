@@ -238,6 +238,7 @@ class OracleTree:
         assert eps.size == self.n_leaf_cells
         if lib().ot_set_eps(self._h, _p(eps)) != 0:
             raise ValueError("eps must be positive")
+        self.eps = eps.copy()
 
     def set_prolong(self, scheme):
         """Prolongation of the coarse-grid correction: 0 linear (1/2,1/4,1/4)
