@@ -153,7 +153,7 @@ int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *pa
  * Dirichlet side it is the value and the ghost 2 b - u.  Periodic applies to
  * both sides of an axis and is a property of the connectivity (Sec. 2.2: the
  * box beyond the last one is the first): those sides carry no boundary faces,
- * and periodicity can only be switched while the tree is the root box alone
+ * and periodicity can only be switched while the tree is its root boxes alone
  * (set it before refining).  At least one side must be Dirichlet (the problem
  * is singular otherwise).  AFG_ERR_ARG for any violation, with the tree
  * unchanged.  Host call; a change discards the device fields, so set rho and
