@@ -268,7 +268,7 @@ def cpu_baseline(problem, tol, steps=1):
 
 
 def run_reference(args):
-    """--impl reference: the oracle (the only reference this build has) on the
+    """--impl reference: the oracle (there is no reference implementation) on the
     host cores, same workload, metric and unit; rank 0 only."""
     from paper_1701_04329_gb300 import workloads as W
     if int(os.environ.get("RANK", "0")) != 0:

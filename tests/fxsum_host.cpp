@@ -1,4 +1,4 @@
-// Host driver for the fixed-point sums of csrc/fxsum.cuh: reads rows of K
+// Host harness for the fixed-point sums of csrc/fxsum.cuh: reads rows of K
 // terms plus one centre value (raw doubles), writes for every row the sum
 // sum_k x_k - C * centre and a flag (1 = handled, 0 = caller falls back).
 #include <cstdio>

@@ -23,10 +23,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def fxhost(tmp_path_factory):
     d = tmp_path_factory.mktemp("fx")
-    exe = str(d / "fxsum_driver")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "fxsum_driver.cpp")],
+    exe = str(d / "fxsum_host")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "fxsum_host.cpp")],
                    check=True)
 
     def run(x, K, C):
@@ -64,7 +64,7 @@ CASES = [(2, 0), (3, 0), (4, 0), (6, 0), (4, 4), (6, 6)]
 
 
 @pytest.mark.parametrize("K,C", CASES)
-def test_close_exponents_are_correctly_rounded(driver, K, C):
+def test_close_exponents_are_correctly_rounded(fxhost, K, C):
     rng = np.random.default_rng(11 + K + C)
     n = 4000
     # terms within a factor 2^G of one another: no bit leaves the window
@@ -73,14 +73,14 @@ def test_close_exponents_are_correctly_rounded(driver, K, C):
     expo = rng.integers(0, G, size=(n, K + 1)) + rng.integers(-40, 40, size=(n, 1))
     sign = rng.choice([-1.0, 1.0], size=(n, K + 1))
     x = sign * np.ldexp(mant, expo)
-    s, ok = driver(x, K, C)
+    s, ok = fxhost(x, K, C)
     assert ok.all()
     for i in range(n):
         assert s[i] == float(exact(x[i], K, C)), (x[i], s[i])
 
 
 @pytest.mark.parametrize("K,C", CASES)
-def test_wide_exponents_within_bound(driver, K, C):
+def test_wide_exponents_within_bound(fxhost, K, C):
     rng = np.random.default_rng(21 + K + C)
     n = 4000
     mant = rng.uniform(1.0, 2.0, size=(n, K + 1))
@@ -89,7 +89,7 @@ def test_wide_exponents_within_bound(driver, K, C):
     x = sign * np.ldexp(mant, expo)
     # exact cancellation in some rows: the result may be tiny or zero
     x[::7, 1] = -x[::7, 0]
-    s, ok = driver(x, K, C)
+    s, ok = fxhost(x, K, C)
     assert ok.all()
     worst = worst64 = 0.0
     for i in range(n):
@@ -111,7 +111,7 @@ def test_wide_exponents_within_bound(driver, K, C):
 
 
 @pytest.mark.parametrize("K,C", CASES)
-def test_ties_round_to_even_and_cancellation(driver, K, C):
+def test_ties_round_to_even_and_cancellation(fxhost, K, C):
     # 1 + 2^-53 is a tie between 1 and 1 + 2^-52: nearest-even gives 1;
     # 1 + 2^-52 + 2^-53 ties to 1 + 2^-51
     rows = []
@@ -124,10 +124,10 @@ def test_ties_round_to_even_and_cancellation(driver, K, C):
     x = np.array(rows)
     if K < 3:   # rows 1, 2 and 4 need three terms
         x = x[[0, 3]]
-        s, ok = driver(x, K, C)
+        s, ok = fxhost(x, K, C)
         assert ok.all() and s[0] == 1.0 and s[1] == 0.0
         return
-    s, ok = driver(x, K, C)
+    s, ok = fxhost(x, K, C)
     assert ok.all()
     assert s[0] == 1.0
     assert s[1] == 1.0 + 2.0 ** -51
@@ -137,7 +137,7 @@ def test_ties_round_to_even_and_cancellation(driver, K, C):
 
 
 @pytest.mark.parametrize("K,C", CASES)
-def test_zero_and_subnormal_terms(driver, K, C):
+def test_zero_and_subnormal_terms(fxhost, K, C):
     rng = np.random.default_rng(31 + K)
     n = 500
     x = rng.normal(size=(n, K + 1))                     # x[:, 0] stays a normal term
@@ -145,7 +145,7 @@ def test_zero_and_subnormal_terms(driver, K, C):
         x[k % 3::3, k] = 0.0
         x[(k + 1) % 3::3, k] = -0.0
         x[(k + 2) % 3::3, k] = 5e-324 * rng.integers(1, 1000, size=len(x[(k + 2) % 3::3]))
-    s, ok = driver(x, K, C)
+    s, ok = fxhost(x, K, C)
     assert ok.all()
     for i in range(n):
         ex = exact(x[i], K, C)
@@ -153,7 +153,7 @@ def test_zero_and_subnormal_terms(driver, K, C):
 
 
 @pytest.mark.parametrize("K,C", CASES)
-def test_unhandled_range_is_reported(driver, K, C):
+def test_unhandled_range_is_reported(fxhost, K, C):
     z = [0.0] * (K + 1)
     rows = [list(z)]                                   # all zero: caller adds in FP64
     r = list(z); r[0] = 1e-300; rows.append(r)         # largest term below 2^-959
@@ -161,11 +161,11 @@ def test_unhandled_range_is_reported(driver, K, C):
     r = list(z); r[0] = math.inf; rows.append(r)
     r = list(z); r[0] = math.nan; rows.append(r)
     r = list(z); r[0] = 1.0; r[1] = math.inf; rows.append(r)
-    s, ok = driver(np.array(rows), K, C)
+    s, ok = fxhost(np.array(rows), K, C)
     assert not ok.any()
     # the edges of the handled range: 2^-959 (biased exponent 64) and 2^1017 (2040)
     r1 = list(z); r1[0] = 2.0 ** -959; r1[1] = 2.0 ** -960
     r2 = list(z); r2[0] = 2.0 ** 1017; r2[1] = -(2.0 ** 1016)
-    s, ok = driver(np.array([r1, r2]), K, C)
+    s, ok = fxhost(np.array([r1, r2]), K, C)
     assert ok.all()
     assert s[0] == 1.5 * 2.0 ** -959 and s[1] == 2.0 ** 1016
