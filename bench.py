@@ -249,6 +249,30 @@ def max_over_ranks(dist, x):
     return float(t.item())
 
 
+def twin_errors(tree, uniform_level, dev, opts):
+    """The manufactured twin of the workload: the same two Gaussians (opposite
+    signs) as the exact solution u, its Laplacian as the source and its face
+    values as Dirichlet data, solved on the same tree (the refinement flags
+    depend only on the sources' positions and width); per precision the max
+    error against u relative to max |u|, with cycles and residual."""
+    import torch
+    from paper_1701_04329_gb300 import workloads as W
+    pt = W.twin3d(uniform_level=uniform_level)
+    rho_t, b_t = pt.data(tree)
+    ue = torch.tensor(pt.u_exact(tree.cell_centers()), device=dev)
+    scale = float(ue.abs().max())
+    res = {"workload": "u = exp(-|x-c1|^2/s^2) - exp(-|x-c2|^2/s^2), rho = Laplacian(u), b = u on the sides; "
+                       "same tree, same tolerance"}
+    for name, o in opts:
+        tree.set_rhs(torch.tensor(rho_t, device=dev))
+        tree.set_dirichlet(torch.tensor(b_t, device=dev))
+        tree.set_solution(torch.zeros_like(ue))
+        st = tree.solve(o)
+        res[name] = {"max_err_rel": float((tree.get_solution() - ue).abs().max()) / scale,
+                     "cycles": st["cycles"], "rel_residual": st["rel_residual"]}
+    return res
+
+
 def cpu_baseline(problem, tol, steps=1):
     """The oracle as it stands, on this host's cores: full solves to `tol`."""
     from oracle.oracle import OracleTree
@@ -407,6 +431,12 @@ def main():
     ms_e2e, _, _ = timed(e2e_step(opts64), args.steps, 1)
     ms_e2e_mx, _, _ = timed(e2e_step(optsmx), args.steps, 1)
 
+    # discretisation error on the manufactured twin (not timed); a failure here only loses this entry
+    try:
+        twin = twin_errors(tree, args.uniform_level, dev, (("fp64", opts64), ("mixed", optsmx)))
+    except Exception as ex:  # noqa: BLE001 - reported in the JSON line instead
+        twin = {"error": str(ex)[:300]}
+
     # roofline: the dominant kernel (red-black half-sweep on the finest uniform level), timed alone
     lvl = max(range(1, info.highest_level + 1), key=lambda l: info.boxes_per_level[l])
     tree.set_rhs(rho)
@@ -455,6 +485,7 @@ def main():
                 "h2d_bytes_per_step": int(rho_h.nbytes + b_h.nbytes), "d2h_bytes_per_step": int(n * 8)},
         "gpu_launches": launches,
         "clocks": clk,
+        "manufactured_twin": twin,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nc, times, cyc, cores = cpu_baseline(p, args.tol)

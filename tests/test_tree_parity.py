@@ -102,3 +102,16 @@ def test_multiroot_adapt_sequences(D, N, roots, types, seed):
         assert a.adapt(flags, nbuf) == b.adapt(flags, nbuf)
         check_tree(same_tree(a, b), D, roots=roots, periodic=periodic)
     assert len(a.face_centers()) == b.n_bfaces
+
+
+def test_manufactured_twin_shares_the_workload_tree():
+    """The bench solves the manufactured twin on the workload's tree: both
+    problems refine by the same flags (positions and width of the two
+    sources), so the library builds the same tree for either."""
+    for lvl in (3, 4):
+        a, b = W.twosrc3d(uniform_level=lvl), W.twin3d(uniform_level=lvl)
+        ta, tb = afgpu.Tree(3, 8, a.max_level), afgpu.Tree(3, 8, b.max_level)
+        a.build(ta)
+        b.build(tb)
+        ea, eb = ta.export(), tb.export()
+        assert all(np.array_equal(ea[k], eb[k]) for k in ("level", "idx", "parent", "children", "neighbours"))
