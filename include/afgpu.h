@@ -4,8 +4,10 @@
  * Teunissen & Ebert, "Afivo" (arXiv:1701.04329).
  *
  * Problem (Sec. 3, Eq. mg-discr-equation): A_h(u_h) = rho_h on [0,1]^D,
- * D = 2 or 3, with Dirichlet data on the domain boundary, discretised on a
- * tree of boxes of N^D cells (Sec. 1.3, 2.1).  The library holds the tree,
+ * D = 2 or 3, with Dirichlet, Neumann or periodic domain sides (at least one
+ * Dirichlet side), discretised on a tree of boxes of N^D cells (Sec. 1.3,
+ * 2.1).  Trees whose level 1 is a block of root boxes (domain [0,r_x] x
+ * [0,r_y] (x [0,r_z])) support the tree calls only, so far.  The library holds the tree,
  * its per-level box lists and all field data on the GPU; every operator of
  * the solve (ghost cells, red-black Gauss-Seidel, residual, restriction,
  * prolongation, norms) is a CUDA kernel of this library.
@@ -48,7 +50,8 @@ extern "C" {
 #define AFG_ERR_NOT_CONVERGED (-5)  /* max_cycles reached above rel_tol (results are valid) */
 #define AFG_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up */
 
-#define AFG_FP64 0   /* all multigrid arithmetic in double precision */
+#define AFG_FP64 0   /* all multigrid arithmetic in double precision (some neighbour sums are formed
+                        exactly in 64-bit fixed point and rounded once: never less accurate) */
 #define AFG_MIXED 1  /* FP64 residual + update around FP32 multigrid (defect correction) */
 
 typedef struct afg_tree afg_tree;
@@ -254,7 +257,9 @@ int afg_kernel_launches(unsigned long long *count);
  * per launch, the cells covered (`cells`) and the algorithmic bytes and
  * flops of one launch.  With s = 8 (FP64) or 4 (FP32) bytes per value, per
  * cell covered: half-sweep 3s/2 bytes (other colour of u, own colour of rho
- * and u written) and (2D+2)/2 flops; residual + restriction 2s + 3s/2^D
+ * and u written) and (2D+1)/2 flops in FP64 (2D-1 additions and one FMA with
+ * the pre-scaled source per update) or (2D+2)/2 in FP32 (and a
+ * multiplication); residual + restriction 2s + 3s/2^D
  * bytes and 2D+5 flops; correction 2s + 2s/2^D bytes and 5 flops; leaf
  * residual 2s + 4 bytes (the FP32 copy of r) and 2D+3 flops.  Field contents
  * are overwritten.  Needs afg_set_rhs first. */
