@@ -1,5 +1,7 @@
-// Template side of the launch layer; instantiated per dimension in
-// launch_d2.cu / launch_d3.cu so the two compile in parallel.
+// Template side of the launch layer; instantiated per dimension (the
+// dispatch, launch_d2.cu / launch_d3.cu) and per dimension and precision (the
+// launches and their kernels, launch_d<D>_f64.cu / launch_d<D>_f32.cu), so
+// that the six translation units compile in parallel.
 #pragma once
 #include <algorithm>
 #include <stdexcept>
@@ -295,53 +297,131 @@ void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin
         }                                                                             \
     } else bad_size(M, MP);
 
+// The precision-specific launches, instantiated per (dimension, precision) in
+// launch_d<D>_f64.cu / launch_d<D>_f32.cu so those compile in parallel.
+template <int D, typename T>
+struct PrecOps {
+    static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh);
+    static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
+                       void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+    static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
+                       const void *rho, const void *rhoh, double h2, int colour, int hom);
+    static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
+                               double ih2, int hom);
+    static void fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
+                    double ih2, int hom, void *rhoh);
+    static void correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold);
+    static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u);
+    static void leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
+                              const void *rho, int hom, unsigned long long *rmax,
+                              unsigned long long *pmax, void *rout, bool rout_f32);
+    static void leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst);
+    static void leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst);
+};
+
+template <int D, typename T>
+void PrecOps<D, T>::rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
+    AFG_SWITCH_M(c.M, (do_rho_hat<D, MM, T>(c, A, list, n, rho, rhoh)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
+                           void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    do_bottom<D, T>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
+                           const void *rho, const void *rhoh, double h2, int colour, int hom) {
+    AFG_SWITCH_M(c.M, (do_smooth<D, MM, T>(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
+                                   double ih2, int hom) {
+    AFG_SWITCH_MMP(c.M, c.MP, (do_resid_restrict<D, MM, PP, T>(c, A, b0, n, u, rho, vold, ih2, hom)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
+                        double ih2, int hom, void *rhoh) {
+    AFG_SWITCH_M(c.M, (do_fas<D, MM, T>(c, A, b0, n, u, rho, vold, ih2, hom, rhoh)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
+    AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, T>(c, A, b0, n, u, vold)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
+    AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, T>(c, A, b0, n, list, u)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
+                                  const void *rho, int hom, unsigned long long *rmax,
+                                  unsigned long long *pmax, void *rout, bool rout_f32) {
+    AFG_SWITCH_M(c.M, (do_leaf_residual<D, MM, T>(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
+    AFG_SWITCH_M(c.M, (do_leaf_set<D, MM, T>(c, A, list, n, src, dst)));
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
+    AFG_SWITCH_M(c.M, (do_leaf_get<D, MM, T>(c, A, list, n, src, dst)));
+}
+
 template <int D>
 struct DimOps {
     static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_rho_hat<D, MM, double>(c, A, list, n, rho, rhoh))); }
-        else { AFG_SWITCH_M(c.M, (do_rho_hat<D, MM, float>(c, A, list, n, rho, rhoh))); }
+        if (c.fp64) PrecOps<D, double>::rho_hat(c, A, list, n, rho, rhoh);
+        else PrecOps<D, float>::rho_hat(c, A, list, n, rho, rhoh);
     }
     static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
-        if (c.fp64) do_bottom<D, double>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
-        else do_bottom<D, float>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+        if (c.fp64) PrecOps<D, double>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+        else PrecOps<D, float>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
     }
     static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
                        const void *rho, const void *rhoh, double h2, int colour, int hom) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_smooth<D, MM, double>(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom))); }
-        else { AFG_SWITCH_M(c.M, (do_smooth<D, MM, float>(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom))); }
+        if (c.fp64) PrecOps<D, double>::smooth(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
+        else PrecOps<D, float>::smooth(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
     }
     static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
                                double ih2, int hom) {
-        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_resid_restrict<D, MM, PP, double>(c, A, b0, n, u, rho, vold, ih2, hom))); }
-        else { AFG_SWITCH_MMP(c.M, c.MP, (do_resid_restrict<D, MM, PP, float>(c, A, b0, n, u, rho, vold, ih2, hom))); }
+        if (c.fp64) PrecOps<D, double>::resid_restrict(c, A, b0, n, u, rho, vold, ih2, hom);
+        else PrecOps<D, float>::resid_restrict(c, A, b0, n, u, rho, vold, ih2, hom);
     }
     static void fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
                     double ih2, int hom, void *rhoh) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_fas<D, MM, double>(c, A, b0, n, u, rho, vold, ih2, hom, rhoh))); }
-        else { AFG_SWITCH_M(c.M, (do_fas<D, MM, float>(c, A, b0, n, u, rho, vold, ih2, hom, rhoh))); }
+        if (c.fp64) PrecOps<D, double>::fas(c, A, b0, n, u, rho, vold, ih2, hom, rhoh);
+        else PrecOps<D, float>::fas(c, A, b0, n, u, rho, vold, ih2, hom, rhoh);
     }
     static void correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
-        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, double>(c, A, b0, n, u, vold))); }
-        else { AFG_SWITCH_MMP(c.M, c.MP, (do_correct<D, MM, PP, float>(c, A, b0, n, u, vold))); }
+        if (c.fp64) PrecOps<D, double>::correct(c, A, b0, n, u, vold);
+        else PrecOps<D, float>::correct(c, A, b0, n, u, vold);
     }
     static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
-        if (c.fp64) { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, double>(c, A, b0, n, list, u))); }
-        else { AFG_SWITCH_MMP(c.M, c.MP, (do_restrict_u<D, MM, PP, float>(c, A, b0, n, list, u))); }
+        if (c.fp64) PrecOps<D, double>::restrict_u(c, A, b0, n, list, u);
+        else PrecOps<D, float>::restrict_u(c, A, b0, n, list, u);
     }
     static void leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
                               const void *rho, int hom, unsigned long long *rmax,
                               unsigned long long *pmax, void *rout, bool rout_f32) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_leaf_residual<D, MM, double>(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32))); }
-        else { AFG_SWITCH_M(c.M, (do_leaf_residual<D, MM, float>(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32))); }
+        if (c.fp64) PrecOps<D, double>::leaf_residual(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);
+        else PrecOps<D, float>::leaf_residual(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);
     }
     static void leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_leaf_set<D, MM, double>(c, A, list, n, src, dst))); }
-        else { AFG_SWITCH_M(c.M, (do_leaf_set<D, MM, float>(c, A, list, n, src, dst))); }
+        if (c.fp64) PrecOps<D, double>::leaf_set(c, A, list, n, src, dst);
+        else PrecOps<D, float>::leaf_set(c, A, list, n, src, dst);
     }
     static void leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
-        if (c.fp64) { AFG_SWITCH_M(c.M, (do_leaf_get<D, MM, double>(c, A, list, n, src, dst))); }
-        else { AFG_SWITCH_M(c.M, (do_leaf_get<D, MM, float>(c, A, list, n, src, dst))); }
+        if (c.fp64) PrecOps<D, double>::leaf_get(c, A, list, n, src, dst);
+        else PrecOps<D, float>::leaf_get(c, A, list, n, src, dst);
     }
     static void bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc) {
         AFG_SWITCH_MMP(c.M, c.MP, (do_bc_restrict<D, MM, PP>(c, A, b0, n, bc)));
@@ -370,5 +450,6 @@ struct DimOps {
         AFG_SWITCH_M(c.M, (do_reduce<D, MM>(c, A, list, n, x, y, mode, partials, result)));
     }
 };
+
 
 }  // namespace afg
