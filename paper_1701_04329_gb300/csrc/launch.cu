@@ -9,6 +9,10 @@ namespace afg {
 
 extern template struct DimOps<2>;
 extern template struct DimOps<3>;
+extern template struct PrecOps<2, double>;
+extern template struct PrecOps<2, float>;
+extern template struct PrecOps<3, double>;
+extern template struct PrecOps<3, float>;
 
 unsigned long long g_launches = 0;
 

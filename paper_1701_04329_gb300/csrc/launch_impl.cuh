@@ -377,79 +377,141 @@ void PrecOps<D, T>::leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *li
 
 template <int D>
 struct DimOps {
-    static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
-        if (c.fp64) PrecOps<D, double>::rho_hat(c, A, list, n, rho, rhoh);
-        else PrecOps<D, float>::rho_hat(c, A, list, n, rho, rhoh);
-    }
+    static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh);
     static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
-                       void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
-        if (c.fp64) PrecOps<D, double>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
-        else PrecOps<D, float>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
-    }
+                       void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
     static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
-                       const void *rho, const void *rhoh, double h2, int colour, int hom) {
-        if (c.fp64) PrecOps<D, double>::smooth(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
-        else PrecOps<D, float>::smooth(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
-    }
+                       const void *rho, const void *rhoh, double h2, int colour, int hom);
     static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
-                               double ih2, int hom) {
-        if (c.fp64) PrecOps<D, double>::resid_restrict(c, A, b0, n, u, rho, vold, ih2, hom);
-        else PrecOps<D, float>::resid_restrict(c, A, b0, n, u, rho, vold, ih2, hom);
-    }
+                               double ih2, int hom);
     static void fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
-                    double ih2, int hom, void *rhoh) {
-        if (c.fp64) PrecOps<D, double>::fas(c, A, b0, n, u, rho, vold, ih2, hom, rhoh);
-        else PrecOps<D, float>::fas(c, A, b0, n, u, rho, vold, ih2, hom, rhoh);
-    }
-    static void correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
-        if (c.fp64) PrecOps<D, double>::correct(c, A, b0, n, u, vold);
-        else PrecOps<D, float>::correct(c, A, b0, n, u, vold);
-    }
-    static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
-        if (c.fp64) PrecOps<D, double>::restrict_u(c, A, b0, n, list, u);
-        else PrecOps<D, float>::restrict_u(c, A, b0, n, list, u);
-    }
+                    double ih2, int hom, void *rhoh);
+    static void correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold);
+    static void restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u);
     static void leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
                               const void *rho, int hom, unsigned long long *rmax,
-                              unsigned long long *pmax, void *rout, bool rout_f32) {
-        if (c.fp64) PrecOps<D, double>::leaf_residual(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);
-        else PrecOps<D, float>::leaf_residual(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);
-    }
-    static void leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
-        if (c.fp64) PrecOps<D, double>::leaf_set(c, A, list, n, src, dst);
-        else PrecOps<D, float>::leaf_set(c, A, list, n, src, dst);
-    }
-    static void leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
-        if (c.fp64) PrecOps<D, double>::leaf_get(c, A, list, n, src, dst);
-        else PrecOps<D, float>::leaf_get(c, A, list, n, src, dst);
-    }
-    static void bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc) {
-        AFG_SWITCH_MMP(c.M, c.MP, (do_bc_restrict<D, MM, PP>(c, A, b0, n, bc)));
-    }
-    static void mixed_update(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *x, const float *e) {
-        AFG_SWITCH_M(c.M, (do_mixed_update<D, MM>(c, A, list, n, x, e)));
-    }
+                              unsigned long long *pmax, void *rout, bool rout_f32);
+    static void leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst);
+    static void leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst);
+    static void bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc);
+    static void mixed_update(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *x, const float *e);
     static void adjoint_apply(const LaunchCfg &c, const BoxMeta &A, const int *child, const double *hb,
-                              const int *list, int n, const double *lam, double *out) {
-        AFG_SWITCH_M(c.M, (do_adjoint_apply<D, MM>(c, A, child, hb, list, n, lam, out)));
-    }
+                              const int *list, int n, const double *lam, double *out);
     static void adjoint_db(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n,
-                           const double *lam, double *db) {
-        AFG_SWITCH_M(c.M, (do_adjoint_db<D, MM>(c, A, hb, list, n, lam, db)));
-    }
+                           const double *lam, double *db);
     static void axpbypcz(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *out, double a,
-                         const double *x, double b, const double *y, double cc, const double *z) {
-        AFG_SWITCH_M(c.M, (do_axpbypcz<D, MM>(c, A, list, n, out, a, x, b, y, cc, z)));
-    }
+                         const double *x, double b, const double *y, double cc, const double *z);
     static void scale(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n, double *out,
-                      const double *x, int power) {
-        AFG_SWITCH_M(c.M, (do_scale<D, MM>(c, A, hb, list, n, out, x, power)));
-    }
+                      const double *x, int power);
     static void reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *x,
-                       const double *y, int mode, double *partials, double *result) {
-        AFG_SWITCH_M(c.M, (do_reduce<D, MM>(c, A, list, n, x, y, mode, partials, result)));
-    }
+                       const double *y, int mode, double *partials, double *result);
 };
+
+template <int D>
+void DimOps<D>::rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh) {
+    if (c.fp64) PrecOps<D, double>::rho_hat(c, A, list, n, rho, rhoh);
+    else PrecOps<D, float>::rho_hat(c, A, list, n, rho, rhoh);
+}
+
+template <int D>
+void DimOps<D>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
+                       void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    if (c.fp64) PrecOps<D, double>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+    else PrecOps<D, float>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+}
+
+template <int D>
+void DimOps<D>::smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
+                       const void *rho, const void *rhoh, double h2, int colour, int hom) {
+    if (c.fp64) PrecOps<D, double>::smooth(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
+    else PrecOps<D, float>::smooth(c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);
+}
+
+template <int D>
+void DimOps<D>::resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
+                               double ih2, int hom) {
+    if (c.fp64) PrecOps<D, double>::resid_restrict(c, A, b0, n, u, rho, vold, ih2, hom);
+    else PrecOps<D, float>::resid_restrict(c, A, b0, n, u, rho, vold, ih2, hom);
+}
+
+template <int D>
+void DimOps<D>::fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
+                    double ih2, int hom, void *rhoh) {
+    if (c.fp64) PrecOps<D, double>::fas(c, A, b0, n, u, rho, vold, ih2, hom, rhoh);
+    else PrecOps<D, float>::fas(c, A, b0, n, u, rho, vold, ih2, hom, rhoh);
+}
+
+template <int D>
+void DimOps<D>::correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
+    if (c.fp64) PrecOps<D, double>::correct(c, A, b0, n, u, vold);
+    else PrecOps<D, float>::correct(c, A, b0, n, u, vold);
+}
+
+template <int D>
+void DimOps<D>::restrict_u(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u) {
+    if (c.fp64) PrecOps<D, double>::restrict_u(c, A, b0, n, list, u);
+    else PrecOps<D, float>::restrict_u(c, A, b0, n, list, u);
+}
+
+template <int D>
+void DimOps<D>::leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
+                              const void *rho, int hom, unsigned long long *rmax,
+                              unsigned long long *pmax, void *rout, bool rout_f32) {
+    if (c.fp64) PrecOps<D, double>::leaf_residual(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);
+    else PrecOps<D, float>::leaf_residual(c, A, list, n, u, rho, hom, rmax, pmax, rout, rout_f32);
+}
+
+template <int D>
+void DimOps<D>::leaf_set(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *src, void *dst) {
+    if (c.fp64) PrecOps<D, double>::leaf_set(c, A, list, n, src, dst);
+    else PrecOps<D, float>::leaf_set(c, A, list, n, src, dst);
+}
+
+template <int D>
+void DimOps<D>::leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *src, double *dst) {
+    if (c.fp64) PrecOps<D, double>::leaf_get(c, A, list, n, src, dst);
+    else PrecOps<D, float>::leaf_get(c, A, list, n, src, dst);
+}
+
+template <int D>
+void DimOps<D>::bc_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, double *bc) {
+    AFG_SWITCH_MMP(c.M, c.MP, (do_bc_restrict<D, MM, PP>(c, A, b0, n, bc)));
+}
+
+template <int D>
+void DimOps<D>::mixed_update(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *x, const float *e) {
+    AFG_SWITCH_M(c.M, (do_mixed_update<D, MM>(c, A, list, n, x, e)));
+}
+
+template <int D>
+void DimOps<D>::adjoint_apply(const LaunchCfg &c, const BoxMeta &A, const int *child, const double *hb,
+                              const int *list, int n, const double *lam, double *out) {
+    AFG_SWITCH_M(c.M, (do_adjoint_apply<D, MM>(c, A, child, hb, list, n, lam, out)));
+}
+
+template <int D>
+void DimOps<D>::adjoint_db(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n,
+                           const double *lam, double *db) {
+    AFG_SWITCH_M(c.M, (do_adjoint_db<D, MM>(c, A, hb, list, n, lam, db)));
+}
+
+template <int D>
+void DimOps<D>::axpbypcz(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, double *out, double a,
+                         const double *x, double b, const double *y, double cc, const double *z) {
+    AFG_SWITCH_M(c.M, (do_axpbypcz<D, MM>(c, A, list, n, out, a, x, b, y, cc, z)));
+}
+
+template <int D>
+void DimOps<D>::scale(const LaunchCfg &c, const BoxMeta &A, const double *hb, const int *list, int n, double *out,
+                      const double *x, int power) {
+    AFG_SWITCH_M(c.M, (do_scale<D, MM>(c, A, hb, list, n, out, x, power)));
+}
+
+template <int D>
+void DimOps<D>::reduce(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const double *x,
+                       const double *y, int mode, double *partials, double *result) {
+    AFG_SWITCH_M(c.M, (do_reduce<D, MM>(c, A, list, n, x, y, mode, partials, result)));
+}
 
 
 }  // namespace afg
