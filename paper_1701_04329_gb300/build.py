@@ -61,7 +61,7 @@ def build(force=False, verbose=False, jobs=None):
         if verbose:
             print(r.stdout + r.stderr)
 
-    with cf.ThreadPoolExecutor(max_workers=jobs or min(8, len(cmds))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=jobs or max(1, min(16, os.cpu_count() or 1, len(cmds)))) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + ".tmp%d" % os.getpid()
     run([cc] + ARCH + ["-shared", "-o", tmp] + objs)
