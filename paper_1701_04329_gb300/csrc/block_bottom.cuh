@@ -60,6 +60,39 @@ AFG_BLK_HD void blk_cell(const BlkLevel &L, long long c, int &i, int &j, int &k)
     k = L.D == 3 ? (int)(c / ((long long)L.n[0] * L.n[1])) + 1 : 0;
 }
 
+// Where a cell and a face cell of the block live in the per-box storage.
+// Box storage is red-black split: the red half (0-based (i + j + k + D)
+// even, i.e. 1-based indices summing to an even number), then the black
+// half, each ordered (k, j, i >> 1) with i >> 1 fastest.
+AFG_BLK_HD int blk_rbi(int D, int M, int i, int j, int k) {  // 0-based within the box
+    const int H = (D == 2 ? M * M : M * M * M) / 2;
+    return ((i + j + k + D) & 1) * H + (k * M + j) * (M / 2) + (i >> 1);
+}
+
+// cell (i, j, k) (1-based, block of boxes of M cells): root index ri +
+// nroot0 (rj + nroot1 rk) and the cell's red-black index within that box
+AFG_BLK_HD void blk_cell_home(int D, int M, const int *nroot, int i, int j, int k, int &root, int &q) {
+    const int ri = (i - 1) / M, rj = (j - 1) / M, rk = D == 3 ? (k - 1) / M : 0;
+    root = ri + nroot[0] * (rj + nroot[1] * rk);
+    q = blk_rbi(D, M, (i - 1) % M, (j - 1) % M, D == 3 ? (k - 1) % M : 0);
+}
+
+// face cell f of side s of the block: root index and the face cell within
+// that box's side (tangential axes lower first, lower fastest)
+AFG_BLK_HD void blk_face_home(const BlkLevel &L, int M, const int *nroot, int s, int f, int &root, int &lf) {
+    int t1, t2;
+    const int a = s / 2;
+    t1 = a == 0 ? 1 : 0;
+    t2 = L.D == 3 ? (a == 2 ? 1 : 2) : -1;
+    const int f1 = f % L.n[t1], f2 = f / L.n[t1];
+    int r[3] = {0, 0, 0};
+    r[a] = (s & 1) ? nroot[a] - 1 : 0;
+    r[t1] = f1 / M;
+    if (t2 >= 0) r[t2] = f2 / M;
+    root = r[0] + nroot[0] * (r[1] + nroot[1] * r[2]);
+    lf = (f1 % M) + M * (t2 >= 0 ? f2 % M : 0);
+}
+
 template <typename T>
 AFG_BLK_HD T blk_nbsum(const BlkLevel &L, const T *v, int i, int j, int k) {
     T s = (v[blk_at(L, i - 1, j, k)] + v[blk_at(L, i + 1, j, k)]) + (v[blk_at(L, i, j - 1, k)] + v[blk_at(L, i, j + 1, k)]);

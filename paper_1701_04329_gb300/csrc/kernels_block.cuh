@@ -18,7 +18,7 @@
 // oracle's cycle bit for bit on the host.
 #pragma once
 #include "block_bottom.cuh"
-#include "kernels_bottom.cuh"  // rbi_rt: red-black index within a box
+#include "kernels.cuh"
 
 namespace afg {
 
@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(kThreads) k_bottom_block(BoxMeta A, BlockTree 
     for (long long c = tid; c < LT.cells; c += nth) {
         int i, j, k;
         blk_cell(LT, c, i, j, k);
-        const int ri = (i - 1) / N, rj = (j - 1) / N, rk = D == 3 ? (k - 1) / N : 0;
-        const int b = B.root_box[ri + B.nroot[0] * (rj + B.nroot[1] * rk)];
-        const long long src = A.coff[b] + rbi_rt(D, N, (i - 1) % N, (j - 1) % N, D == 3 ? (k - 1) % N : 0);
+        int root, q;
+        blk_cell_home(D, N, B.nroot, i, j, k, root, q);
+        const long long src = A.coff[B.root_box[root]] + q;
         const long long g = blk_at(LT, i, j, k);
         fu[top][g] = u[src];
         frho[top][g] = rho[src];
@@ -101,15 +101,11 @@ __global__ void __launch_bounds__(kThreads) k_bottom_block(BoxMeta A, BlockTree 
     for (int s = 0; s < 2 * D; ++s) {
         if (B.bct[s] == 2) continue;
         int t1, t2;
-        const int nf = blk_faces(LT, s, t1, t2), a = s / 2;
+        const int nf = blk_faces(LT, s, t1, t2);
         for (int f = tid; f < nf; f += nth) {
-            const int f1 = f % LT.n[t1], f2 = f / LT.n[t1];
-            int r[3] = {0, 0, 0};
-            r[a] = (s & 1) ? B.nroot[a] - 1 : 0;
-            r[t1] = f1 / N;
-            if (t2 >= 0) r[t2] = f2 / N;
-            const int b = B.root_box[r[0] + B.nroot[0] * (r[1] + B.nroot[1] * r[2])];
-            const int lf = (f1 % N) + N * (t2 >= 0 ? f2 % N : 0);  // face cell within the box side
+            int root, lf;
+            blk_face_home(LT, N, B.nroot, s, f, root, lf);
+            const int b = B.root_box[root];
             wbc[top][s][f] = hom ? T(0) : T(A.bc[A.nbase[b * 2 * D + s] + lf]);
         }
     }
@@ -191,9 +187,9 @@ __global__ void __launch_bounds__(kThreads) k_bottom_block(BoxMeta A, BlockTree 
     for (long long c = tid; c < LT.cells; c += nth) {
         int i, j, k;
         blk_cell(LT, c, i, j, k);
-        const int ri = (i - 1) / N, rj = (j - 1) / N, rk = D == 3 ? (k - 1) / N : 0;
-        const int b = B.root_box[ri + B.nroot[0] * (rj + B.nroot[1] * rk)];
-        const long long dst = A.coff[b] + rbi_rt(D, N, (i - 1) % N, (j - 1) % N, D == 3 ? (k - 1) % N : 0);
+        int root, q;
+        blk_cell_home(D, N, B.nroot, i, j, k, root, q);
+        const long long dst = A.coff[B.root_box[root]] + q;
         const long long g = blk_at(LT, i, j, k);
         u[dst] = fu[top][g];
         if (mode == 1) vold[dst] = fv[top][g];
