@@ -253,3 +253,148 @@ AFG_BLK_HD void blk_bc_restrict(const BlkLevel &F, const BlkLevel &C, int s, con
 }
 
 }  // namespace afg
+
+// ---- variable coefficients (Sec. 3.4-3.5) ----------------------------------
+// op 1: div(eps grad u) with face coefficient 2 e1 e2 / (e1 + e2); op 2: the
+// same in (r,z) coordinates (2D, r = x, the -x side is the axis), r-faces
+// weighted by r_face / r_cell and every restriction weighted by the
+// children's volumes (r at their centres).  eps holds the coefficient with
+// its ghosts (mirrored at the domain sides, wrapped on periodic ones).  M is
+// the box size of the level: radii are formed from the cell's root box
+// origin, as the per-box operators form them.
+
+namespace afg {
+
+// radius (x) of cell i (1-based over the block) and of its two x-faces
+AFG_BLK_HD void blk_radii(const BlkLevel &L, int M, int i, double &rc, double &rm, double &rp) {
+    const int ri = (i - 1) / M, il = (i - 1) % M + 1;
+    const double x0 = (double)ri;
+    rc = x0 + (il - 0.5) * L.h;
+    rm = x0 + (il - 1) * L.h;
+    rp = x0 + il * L.h;
+}
+
+template <typename T>
+AFG_BLK_HD void blk_face_coef(const BlkLevel &L, int M, int op, const T *eps, int i, int j, int k, T *c) {
+    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+    const T e0 = eps[blk_at(L, i, j, k)];
+    for (int s = 0; s < 2 * L.D; ++s) {
+        const T en = eps[blk_at(L, nb[s][0], nb[s][1], nb[s][2])];
+        c[s] = T(2) * e0 * en / (e0 + en);
+    }
+    if (op == 2) {
+        double rc, rm, rp;
+        blk_radii(L, M, i, rc, rm, rp);
+        c[0] *= T(rm / rc);
+        c[1] *= T(rp / rc);
+    }
+}
+
+// sum_s c_s v_s and sum_s c_s over the faces of cell (i,j,k), in side order
+template <typename T>
+AFG_BLK_HD void blk_wsum(const BlkLevel &L, int M, int op, const T *eps, const T *v, int i, int j, int k, T &sv,
+                         T &sc) {
+    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+    T c[6];
+    blk_face_coef(L, M, op, eps, i, j, k, c);
+    T a = T(0), b = T(0);
+    for (int s = 0; s < 2 * L.D; ++s) {
+        a += c[s] * v[blk_at(L, nb[s][0], nb[s][1], nb[s][2])];
+        b += c[s];
+    }
+    sv = a;
+    sc = b;
+}
+
+// (sum_s c_s (v_s - v)) / h^2, evaluated as (sum c_s v_s - sum c_s v) / h^2
+template <typename T>
+AFG_BLK_HD T blk_lap_v(const BlkLevel &L, int M, int op, const T *eps, const T *v, int i, int j, int k) {
+    T sv, sc;
+    blk_wsum(L, M, op, eps, v, i, j, k, sv, sc);
+    const T h = T(L.h);
+    return (sv - sc * v[blk_at(L, i, j, k)]) / (h * h);
+}
+
+// ghosts of the coefficient: mirrored at the domain sides, wrapped on periodic ones
+template <typename T>
+AFG_BLK_HD void blk_fill_eps_ghosts(const BlkLevel &L, T *eps, const int *bct, int tid, int nth) {
+    for (int s = 0; s < 2 * L.D; ++s) {
+        int t1, t2;
+        const int nf = blk_faces(L, s, t1, t2), a = s / 2;
+        for (int f = tid; f < nf; f += nth) {
+            int q[3] = {0, 0, 0};
+            q[t1] = f % L.n[t1] + 1;
+            if (t2 >= 0) q[t2] = f / L.n[t1] + 1;
+            int g[3] = {q[0], q[1], q[2]}, o[3] = {q[0], q[1], q[2]};
+            g[a] = (s & 1) ? L.n[a] + 1 : 0;
+            if (bct[s] == 2) o[a] = (s & 1) ? 1 : L.n[a];
+            else o[a] = (s & 1) ? L.n[a] : 1;
+            eps[blk_at(L, g[0], g[1], g[2])] = eps[blk_at(L, o[0], o[1], o[2])];
+        }
+    }
+}
+
+// local solve of the variable-coefficient equation: u = (sum c_s u_s - h^2 rho) / sum c_s
+template <typename T>
+AFG_BLK_HD void blk_gsrb_v(const BlkLevel &L, int M, int op, const T *eps, T *u, const T *rho, int colour, int tid,
+                           int nth) {
+    const T h2 = T(L.h) * T(L.h);
+    for (long long c = tid; c < L.cells; c += nth) {
+        int i, j, k;
+        blk_cell(L, c, i, j, k);
+        if ((i + j + k) % 2 != colour) continue;
+        const long long g = blk_at(L, i, j, k);
+        T sv, sc;
+        blk_wsum(L, M, op, eps, u, i, j, k, sv, sc);
+        u[g] = (sv - h2 * rho[g]) / sc;
+    }
+}
+
+template <typename T>
+AFG_BLK_HD void blk_residual_v(const BlkLevel &L, int M, int op, const T *eps, const T *u, const T *rho, T *r, int tid,
+                               int nth) {
+    for (long long c = tid; c < L.cells; c += nth) {
+        int i, j, k;
+        blk_cell(L, c, i, j, k);
+        const long long g = blk_at(L, i, j, k);
+        r[g] = rho[g] - blk_lap_v(L, M, op, eps, u, i, j, k);
+    }
+}
+
+template <typename T>
+AFG_BLK_HD void blk_fas_v(const BlkLevel &L, int M, int op, const T *eps, const T *u, const T *rr, T *rho, int tid,
+                          int nth) {
+    for (long long c = tid; c < L.cells; c += nth) {
+        int i, j, k;
+        blk_cell(L, c, i, j, k);
+        const long long g = blk_at(L, i, j, k);
+        rho[g] = rr[g] + blk_lap_v(L, M, op, eps, u, i, j, k);
+    }
+}
+
+// restriction: the plain mean (op 0, 1) or, in (r,z), the mean weighted by
+// the children's radii, summed y then x (Mf = the fine level's box size)
+template <typename T>
+AFG_BLK_HD void blk_restrict_v(const BlkLevel &F, const BlkLevel &C, int Mf, int op, const T *vf, T *vc, int tid,
+                               int nth) {
+    if (op != 2) {
+        blk_restrict(F, C, vf, vc, tid, nth);
+        return;
+    }
+    for (long long c = tid; c < C.cells; c += nth) {
+        int I, J, K;
+        blk_cell(C, c, I, J, K);
+        T s = T(0), w = T(0);
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const int fi = 2 * I - 1 + dx;
+                double rc, rm, rp;
+                blk_radii(F, Mf, fi, rc, rm, rp);
+                s += T(rc) * vf[blk_at(F, fi, 2 * J - 1 + dy, 0)];
+                w += T(rc);
+            }
+        vc[blk_at(C, I, J, K)] = s / w;
+    }
+}
+
+}  // namespace afg

@@ -1,9 +1,10 @@
 // Host harness for csrc/block_bottom.cuh: the part of the multigrid cycle at
 // and below level 1 of a tree whose level 1 is a block of root boxes, run
 // with one thread.  Input (binary, doubles unless noted): int32 header
-// D, N, nr[3], bct[6], mode (0 one V-cycle, 1 one FMG cycle), nd, nu, nb;
-// then level-1 rho and u (rectangle order with ghosts dropped: n0 x n1 (x n2),
-// x fastest) and the face data of every non-periodic side (f1 + n[t1] f2).
+// D, N, nr[3], bct[6], mode (0 one V-cycle, 1 one FMG cycle), nd, nu, nb, op
+// (0 Laplacian, 1 div(eps grad), 2 the same in (r,z)); then level-1 rho, u
+// and eps (rectangle order with ghosts dropped: n0 x n1 (x n2), x fastest)
+// and the face data of every non-periodic side (f1 + n[t1] f2).
 // Output: level-1 u in the same order.
 #include <cstdio>
 #include <cstdlib>
@@ -16,11 +17,12 @@ typedef std::vector<double> Vec;
 
 struct Lev {
     BlkLevel L;
-    Vec u, rho, vold, r, rr, d;
+    Vec u, rho, vold, r, rr, d, eps;
+    int M;
     Vec bc[6];
 };
 
-static int D, N, nr[3], bct[6], mode, nd, nu, nb;
+static int D, N, nr[3], bct[6], mode, nd, nu, nb, op;
 static std::vector<Lev> lv;  // index 0 = coarsest (M = 2), last = level 1 (M = N)
 
 static const double *const *bcp(Lev &l, const double **buf) {
@@ -35,14 +37,16 @@ static void smooth(int li, int n) {
     for (int it = 0; it < n; ++it)
         for (int c = 0; c < 2; ++c) {
             ghosts(lv[li], lv[li].u, false);
-            blk_gsrb(lv[li].L, lv[li].u.data(), lv[li].rho.data(), c, 0, 1);
+            if (op) blk_gsrb_v(lv[li].L, lv[li].M, op, lv[li].eps.data(), lv[li].u.data(), lv[li].rho.data(), c, 0, 1);
+            else blk_gsrb(lv[li].L, lv[li].u.data(), lv[li].rho.data(), c, 0, 1);
         }
 }
 static void fas_coarse(int li) {
     Lev &c = lv[li];
     ghosts(c, c.u, false);
     blk_copy(c.L, c.vold.data(), c.u.data(), 0, 1);
-    blk_fas(c.L, c.u.data(), c.rr.data(), c.rho.data(), 0, 1);
+    if (op) blk_fas_v(c.L, c.M, op, c.eps.data(), c.u.data(), c.rr.data(), c.rho.data(), 0, 1);
+    else blk_fas(c.L, c.u.data(), c.rr.data(), c.rho.data(), 0, 1);
 }
 static void correct(int li) {  // fine level li from li - 1
     Lev &c = lv[li - 1], &f = lv[li];
@@ -50,12 +54,19 @@ static void correct(int li) {  // fine level li from li - 1
     ghosts(c, c.d, true);
     blk_correct(f.L, c.L, f.u.data(), c.d.data(), 0, 1);
 }
+static void residual(Lev &f) {
+    if (op) blk_residual_v(f.L, f.M, op, f.eps.data(), f.u.data(), f.rho.data(), f.r.data(), 0, 1);
+    else blk_residual(f.L, f.u.data(), f.rho.data(), f.r.data(), 0, 1);
+}
+static void restrict_to(Lev &f, Lev &c, const Vec &vf, Vec &vc) {
+    blk_restrict_v(f.L, c.L, f.M, op, vf.data(), vc.data(), 0, 1);
+}
 static void down(int li) {  // residual of li restricted into li - 1, coarse rhs
     Lev &f = lv[li], &c = lv[li - 1];
     ghosts(f, f.u, false);
-    blk_residual(f.L, f.u.data(), f.rho.data(), f.r.data(), 0, 1);
-    blk_restrict(f.L, c.L, f.u.data(), c.u.data(), 0, 1);
-    blk_restrict(f.L, c.L, f.r.data(), c.rr.data(), 0, 1);
+    residual(f);
+    restrict_to(f, c, f.u, c.u);
+    restrict_to(f, c, f.r, c.rr);
     fas_coarse(li - 1);
 }
 static void vcycle_from(int top) {
@@ -74,21 +85,23 @@ int main(int argc, char **argv) {
     if (argc != 3) return 2;
     FILE *in = fopen(argv[1], "rb");
     if (!in) return 3;
-    int hdr[15];
-    if (fread(hdr, sizeof(int), 15, in) != 15) return 4;
+    int hdr[16];
+    if (fread(hdr, sizeof(int), 16, in) != 16) return 4;
     D = hdr[0]; N = hdr[1];
     for (int a = 0; a < 3; ++a) nr[a] = hdr[2 + a];
     for (int s = 0; s < 6; ++s) bct[s] = hdr[5 + s];
-    mode = hdr[11]; nd = hdr[12]; nu = hdr[13]; nb = hdr[14];
+    mode = hdr[11]; nd = hdr[12]; nu = hdr[13]; nb = hdr[14]; op = hdr[15];
     for (int M = 2; M <= N; M *= 2) {
         Lev l;
         l.L = blk_level(D, nr, M);
+        l.M = M;
         for (Vec *v : {&l.u, &l.rho, &l.vold, &l.r, &l.rr, &l.d}) v->assign(l.L.padded, 0.0);
+        l.eps.assign(l.L.padded, 1.0);
         lv.push_back(l);
     }
     Lev &top = lv.back();
     const int nl = (int)lv.size();
-    for (Vec *v : {&top.rho, &top.u})
+    for (Vec *v : {&top.rho, &top.u, &top.eps})
         for (long long c = 0; c < top.L.cells; ++c) {
             int i, j, k;
             blk_cell(top.L, c, i, j, k);
@@ -106,15 +119,18 @@ int main(int argc, char **argv) {
             }
         }
     fclose(in);
+    // the coefficient on every level: restricted down, then its ghosts
+    for (int li = nl - 1; li > 0; --li) restrict_to(lv[li], lv[li - 1], lv[li].eps, lv[li - 1].eps);
+    for (int li = 0; li < nl; ++li) blk_fill_eps_ghosts(lv[li].L, lv[li].eps.data(), bct, 0, 1);
     if (mode == 0) {
         vcycle_from(nl - 1);
     } else {  // FMG: restrict u down, coarse right-hand sides, then up level by level
-        for (int li = nl - 1; li > 0; --li) blk_restrict(lv[li].L, lv[li - 1].L, lv[li].u.data(), lv[li - 1].u.data(), 0, 1);
+        for (int li = nl - 1; li > 0; --li) restrict_to(lv[li], lv[li - 1], lv[li].u, lv[li - 1].u);
         for (int li = nl - 1; li > 0; --li) {
             Lev &f = lv[li], &c = lv[li - 1];
             ghosts(f, f.u, false);
-            blk_residual(f.L, f.u.data(), f.rho.data(), f.r.data(), 0, 1);
-            blk_restrict(f.L, c.L, f.r.data(), c.rr.data(), 0, 1);
+            residual(f);
+            restrict_to(f, c, f.r, c.rr);
             fas_coarse(li - 1);
         }
         for (int li = 0; li < nl; ++li) {

@@ -36,13 +36,17 @@ def rect_index(x, h, n):
     return lin
 
 
-def run(harness, D, N, roots, types, mode, seed, nd=2, nu=2, nb=4):
+def run(harness, D, N, roots, types, mode, seed, nd=2, nu=2, nb=4, op=0):
     exe, d = harness
     t = OracleTree(D, N, 1, roots=roots)
     bct = list(types) if types is not None else [0] * (2 * D)
     if types is not None:
         t.set_boundary_types(types)
     rng = np.random.default_rng(seed)
+    eps = np.exp(rng.normal(size=t.n_leaf_cells)) if op else np.ones(t.n_leaf_cells)
+    if op:
+        t.set_operator(op)
+        t.set_eps(eps)
     rho = rng.normal(size=t.n_leaf_cells)
     b = rng.normal(size=t.n_bfaces)
     u0 = 0.1 * rng.normal(size=t.n_leaf_cells)
@@ -58,6 +62,8 @@ def run(harness, D, N, roots, types, mode, seed, nd=2, nu=2, nb=4):
     rrho = np.zeros(t.n_leaf_cells)
     ru0 = np.zeros(t.n_leaf_cells)
     rrho[lin], ru0[lin] = rho, u0
+    reps = np.zeros(t.n_leaf_cells)
+    reps[lin] = eps
     fc = t.face_centers()
     faces = []
     for s in range(2 * D):
@@ -73,12 +79,13 @@ def run(harness, D, N, roots, types, mode, seed, nd=2, nu=2, nb=4):
         arr = np.zeros(int(on.sum()))
         arr[f] = b[on]
         faces.append(arr)
-    hdr = np.array([D, N] + list(roots) + [1] * (3 - D) + bct + [0] * (6 - 2 * D) + [mode, nd, nu, nb], np.int32)
+    hdr = np.array([D, N] + list(roots) + [1] * (3 - D) + bct + [0] * (6 - 2 * D) + [mode, nd, nu, nb, op], np.int32)
     fin, fout = str(d / "in.bin"), str(d / "out.bin")
     with open(fin, "wb") as f:
         f.write(hdr.tobytes())
         f.write(rrho.tobytes())
         f.write(ru0.tobytes())
+        f.write(reps.tobytes())
         for arr in faces:
             f.write(arr.tobytes())
     subprocess.run([exe, fin, fout], check=True)
@@ -102,3 +109,14 @@ def test_block_grids_match_the_oracle_bit_for_bit(harness, D, N, roots, types, m
 def test_other_smoothing_counts(harness):
     uo, ub = run(harness, 2, 8, (3, 1), [0, 1, 0, 0], 0, seed=3, nd=1, nu=3, nb=6)
     assert np.array_equal(uo, ub)
+
+
+@pytest.mark.parametrize("D,N,roots,types,op", [(2, 8, (2, 1), None, 1), (2, 8, (3, 2), [0, 1, 2, 2], 1),
+                                                (3, 4, (2, 1, 1), [0, 0, 0, 1, 2, 2], 1), (2, 8, (2, 1), None, 2),
+                                                (2, 16, (1, 2), [0, 0, 0, 1], 2)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_variable_coefficient_block_grids_match_the_oracle(harness, D, N, roots, types, op, mode):
+    """div(eps grad u) with a random positive eps per cell, and its (r,z)
+    form (volume-weighted restriction, radii from each root's origin)."""
+    uo, ub = run(harness, D, N, roots, types, mode, seed=31 + N + op + mode, op=op)
+    assert np.array_equal(uo, ub), np.abs(uo - ub).max()
