@@ -6,8 +6,8 @@
  * Problem (Sec. 3, Eq. mg-discr-equation): A_h(u_h) = rho_h on [0,1]^D,
  * D = 2 or 3, with Dirichlet, Neumann or periodic domain sides (at least one
  * Dirichlet side), discretised on a tree of boxes of N^D cells (Sec. 1.3,
- * 2.1).  Trees whose level 1 is a block of root boxes (domain [0,r_x] x
- * [0,r_y] (x [0,r_z])) support the tree calls only, so far.  The library holds the tree,
+ * 2.1).  A tree's level 1 may be a block of root boxes (domain [0,r_x] x
+ * [0,r_y] (x [0,r_z])).  The library holds the tree,
  * its per-level box lists and all field data on the GPU; every operator of
  * the solve (ghost cells, red-black Gauss-Seidel, residual, restriction,
  * prolongation, norms) is a CUDA kernel of this library.
@@ -105,10 +105,11 @@ int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out);
  * ints, each in [1, 64]) root boxes per axis, each the unit square/cube, so
  * the domain is [0,nroot[0]] x [0,nroot[1]] (x [0,nroot[2]]).  Root boxes
  * come first in the canonical box order (Morton order of their indices).
- * The tree calls (refine, adapt, boundary types, export, centres) accept such
- * trees; the multigrid calls (set_rhs onwards) return AFG_ERR_STATE for them
- * when nroot is not all ones.  Also AFG_ERR_ARG when nroot[a] << (max_level-1)
- * exceeds 2^21. */
+ * Every call accepts such trees: below level 1 the coarse grids hold one box
+ * per root, solved together in one CTA (Sec. 3.2), which takes up to about
+ * 16 roots of 8^3 boxes in 3D FP64 (larger blocks fail with AFG_ERR_STATE at
+ * the first multigrid call); forests of them are refused (AFG_ERR_STATE).
+ * AFG_ERR_ARG when nroot[a] << (max_level-1) exceeds 2^21. */
 int afg_tree_create_roots(int dim, int box_n, int max_level, const int *nroot, afg_tree **out);
 int afg_tree_destroy(afg_tree *t);
 

@@ -6,9 +6,9 @@
  * parallelization and geometric multigrid methods" (arXiv:1701.04329):
  * the quadtree/octree of boxes (Sec. 2.1-2.3), ghost cells (Sec. 2.4, 3.3),
  * prolongation/restriction (Sec. 2.5) and the FAS V-cycle / FMG multigrid
- * solver with red-black Gauss-Seidel smoothing (Sec. 3.1-3.2); also the
- * parts the CUDA library does not have yet: domains of several root boxes
- * (Sec. 2.2), the variable-coefficient and (r,z) operators (Sec. 3.4-3.5),
+ * solver with red-black Gauss-Seidel smoothing (Sec. 3.1-3.2), on domains
+ * of one or several root boxes (Sec. 2.2); also the parts the CUDA library
+ * does not have yet: the variable-coefficient and (r,z) operators (Sec. 3.4-3.5),
  * edge/corner ghosts with the bilinear / trilinear and zeroth-order
  * prolongation (Sec. 2.4-2.5), and the field transfer of mesh adaptation
  * (Sec. 2.3).  Every function is pinned by the tests against values fixed

@@ -141,7 +141,7 @@ class Tree:
     """A quadtree (dim=2) or octree (dim=3) on [0,1]^dim, root box of box_n^dim
     cells (Sec. 2.1-2.2), with its multigrid data on the GPU.  roots=(rx, ry[,
     rz]) makes level 1 a block of root boxes, the domain [0,rx] x [0,ry] (x
-    [0,rz]); such trees support the tree calls, not yet the multigrid calls."""
+    [0,rz]) (not in forests)."""
 
     def __init__(self, dim, box_n, max_level, roots=None):
         self.D, self.N, self.max_level = dim, box_n, max_level

@@ -41,14 +41,15 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     // coarse grids, solved in one block); a block of several root boxes needs
     // coarse levels of several connected boxes, which the device path lacks
     for (const HostTree *h : trees)
-        if (h->nroots() != 1)
-            throw std::runtime_error("multigrid on a tree of several root boxes is not available on the GPU; "
-                                     "the tree calls (refine, adapt, export, centres) are");
+        if (h->nroots() != 1 && trees.size() > 1)
+            throw std::runtime_error("a forest cannot hold trees of several root boxes");
     D = trees[0]->D;
     N = trees[0]->N;
     T = (int)trees.size();
+    block = trees[0]->nroots() != 1;
     int nsub = 0;
-    for (int m = N / 2; m >= 2; m /= 2) ++nsub;
+    if (!block)
+        for (int m = N / 2; m >= 2; m /= 2) ++nsub;
     lmin = 1 - nsub;
     lmax = 1;
     tree_top.resize(T);
@@ -114,7 +115,7 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
             const int g = gid[t][b];
             tree[g] = t;
             if (hx.level == 1) {
-                parent[g] = sub[t][nsub - 1];
+                parent[g] = nsub > 0 ? sub[t][nsub - 1] : -1;
             } else {
                 parent[g] = gid[t][hx.parent];
                 int p = 0;
@@ -178,6 +179,17 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     }
 
     auto &own = owned;
+    if (block) {  // the roots' box ids in block order
+        const HostTree &ht = *trees[0];
+        for (int a = 0; a < 3; ++a) block_nroot[a] = ht.nr[a];
+        for (int s2 = 0; s2 < 6; ++s2) block_bct[s2] = ht.bct[s2];
+        std::vector<int> rb(ht.nroots(), -1);
+        for (int b = ht.lstart[1]; b < ht.lstart[1] + ht.lcount[1]; ++b) {
+            const HBox &hx = ht.boxes[b];
+            rb[(hx.idx[0] - 1) + ht.nr[0] * ((hx.idx[1] - 1) + ht.nr[1] * (D == 3 ? hx.idx[2] - 1 : 0))] = gid[0][b];
+        }
+        d_root_box = upload(rb, own);
+    }
     meta.nb = upload(nb, own);
     meta.nmask = upload(nmask, own);
     meta.parent = upload(parent, own);
@@ -305,6 +317,11 @@ void Grid::down_step(Workspace &w, int l, int hom, const int *active, cudaStream
 void Grid::bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
     BoxMeta A = meta;
     A.active = active;
+    if (block) {  // one tree: level 1 and the grids below it in one CTA
+        launch_bottom_block(cfg(1, w.fp64, s), A, block_nroot, block_bct, d_root_box, N, mode, w.u->p, w.rho->p,
+                            w.vold->p, o.n_down, o.n_up, o.n_base, hom);
+        return;
+    }
     int b0[4] = {0, 0, 0, 0};
     for (int l = lmin; l <= 1; ++l) b0[l - lmin] = L(l).b0;
     launch_bottom(cfg(1, w.fp64, s), A, T, N, lmin, ltop, mode, w.u->p, w.rho->p, w.vold->p, o.n_down, o.n_up,

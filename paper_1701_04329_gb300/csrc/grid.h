@@ -61,6 +61,11 @@ class Grid {
     };
 
     int D, N, T, lmin, lmax;
+    // a single tree whose level 1 is a block of root boxes: no device boxes
+    // below level 1 (the block bottom solve keeps those grids in shared memory)
+    bool block = false;
+    int block_nroot[3] = {1, 1, 1}, block_bct[6] = {0, 0, 0, 0, 0, 0};
+    int *d_root_box = nullptr;  // box id of root ri + nroot0 (rj + nroot1 rk)
     std::vector<Level> lv;
     Level &L(int l) { return lv[l - lmin]; }
     int nbox = 0, n_leaf_boxes = 0;

@@ -13,9 +13,8 @@
 //         u_l, correction from l-1 (l above the coarsest), V-cycle from l;
 //         level 1's v' is written back for the FMG correction of level 2.
 //
-// Not yet called by the cycle drivers (the multigrid calls refuse trees of
-// several root boxes until it is); the steps themselves reproduce the
-// oracle's cycle bit for bit on the host.
+// The steps reproduce the oracle's cycle bit for bit on the host; the
+// kernel is what the cycle drivers call at level 1 for such trees.
 #pragma once
 #include "block_bottom.cuh"
 #include "kernels.cuh"

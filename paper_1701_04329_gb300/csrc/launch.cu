@@ -47,6 +47,10 @@ void launch_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int 
                    void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
     AFG_BY_DIM(bottom, c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
 }
+void launch_bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct, const int *root_box,
+                         int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom) {
+    AFG_BY_DIM(bottom_block, c, A, nroot, bct, root_box, N, mode, u, rho, vold, nd, nu, nb, hom);
+}
 void launch_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
                    const void *rhoh, double h2, int colour, int hom) {
     AFG_BY_DIM(smooth, c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);

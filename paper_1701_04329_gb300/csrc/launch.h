@@ -24,6 +24,13 @@ extern unsigned long long g_launches;
 // lvl_b0[li] = first box of level lmin + li
 void launch_bottom(const LaunchCfg &, const BoxMeta &, int ntrees, int N, int lmin, int ltop, int mode, void *u,
                    void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+// the levels at and below level 1 of one tree whose level 1 is a block of
+// root boxes (one CTA): nroot[3] roots per axis, bct[6] side types,
+// root_box (device) the box id of root ri + nroot0 (rj + nroot1 rk); mode 0 =
+// V-cycle from level 1, mode 1 = the FMG steps up to level 1.  Throws when
+// the block's grids do not fit one CTA's shared memory.
+void launch_bottom_block(const LaunchCfg &, const BoxMeta &, const int *nroot, const int *bct, const int *root_box,
+                         int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom);
 // rhoh (may be null): use the pre-scaled source -h^2 rho/(2D) instead of rho
 void launch_smooth(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u, const void *rho,
                    const void *rhoh, double h2, int colour, int hom);

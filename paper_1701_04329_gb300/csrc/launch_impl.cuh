@@ -11,6 +11,7 @@
 #include "kernels_smooth.cuh"
 #include "kernels_full.cuh"
 #include "kernels_bottom.cuh"
+#include "kernels_block.cuh"
 #include "launch.h"
 
 namespace afg {
@@ -265,6 +266,23 @@ void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin
     ++g_launches;
 }
 
+template <int D, typename T>
+void do_bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct, const int *root_box,
+                     int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom) {
+    BlockTree B;
+    for (int a = 0; a < 3; ++a) B.nroot[a] = a < D ? nroot[a] : 1;
+    for (int s = 0; s < 6; ++s) B.bct[s] = s < 2 * D ? bct[s] : 0;
+    B.root_box = root_box;
+    const size_t smem = block_bottom_smem<D, T>(N, B);
+    if (smem > 227 * 1024)
+        throw std::runtime_error("the block of root boxes is too large for one CTA's shared memory (" +
+                                 std::to_string(smem) + " bytes)");
+    auto k = k_bottom_block<D, T>;
+    occupancy(reinterpret_cast<const void *>(k), smem);  // sets the shared-memory limit once
+    launch_pdl(k, 1, smem, c.stream, A, B, N, mode, (T *)u, (T *)rho, (T *)vold, nd, nu, nb, hom);
+    ++g_launches;
+}
+
 // ---- dispatch over the box size --------------------------------------------
 [[noreturn]] inline void bad_size(int M, int MP) {
     throw std::runtime_error("unsupported box size " + std::to_string(M) + "/" + std::to_string(MP));
@@ -304,6 +322,9 @@ struct PrecOps {
     static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh);
     static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+    static void bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct,
+                             const int *root_box, int N, int mode, void *u, void *rho, void *vold, int nd, int nu,
+                             int nb, int hom);
     static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
                        const void *rho, const void *rhoh, double h2, int colour, int hom);
     static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
@@ -328,6 +349,13 @@ template <int D, typename T>
 void PrecOps<D, T>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
                            void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
     do_bottom<D, T>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+}
+
+template <int D, typename T>
+void PrecOps<D, T>::bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct,
+                                 const int *root_box, int N, int mode, void *u, void *rho, void *vold, int nd, int nu,
+                                 int nb, int hom) {
+    do_bottom_block<D, T>(c, A, nroot, bct, root_box, N, mode, u, rho, vold, nd, nu, nb, hom);
 }
 
 template <int D, typename T>
@@ -380,6 +408,9 @@ struct DimOps {
     static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh);
     static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+    static void bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct,
+                             const int *root_box, int N, int mode, void *u, void *rho, void *vold, int nd, int nu,
+                             int nb, int hom);
     static void smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u,
                        const void *rho, const void *rhoh, double h2, int colour, int hom);
     static void resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho, void *vold,
@@ -418,6 +449,14 @@ void DimOps<D>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, 
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
     if (c.fp64) PrecOps<D, double>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
     else PrecOps<D, float>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+}
+
+template <int D>
+void DimOps<D>::bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct,
+                             const int *root_box, int N, int mode, void *u, void *rho, void *vold, int nd, int nu,
+                             int nb, int hom) {
+    if (c.fp64) PrecOps<D, double>::bottom_block(c, A, nroot, bct, root_box, N, mode, u, rho, vold, nd, nu, nb, hom);
+    else PrecOps<D, float>::bottom_block(c, A, nroot, bct, root_box, N, mode, u, rho, vold, nd, nu, nb, hom);
 }
 
 template <int D>
