@@ -47,6 +47,8 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     N = trees[0]->N;
     T = (int)trees.size();
     block = trees[0]->nroots() != 1;
+    if (block && bottom_block_smem(trees[0]->D, true, trees[0]->N, trees[0]->nr, trees[0]->bct) > 227 * 1024)
+        throw std::runtime_error("the block of root boxes is too large for the one-CTA bottom solve");
     int nsub = 0;
     if (!block)
         for (int m = N / 2; m >= 2; m /= 2) ++nsub;

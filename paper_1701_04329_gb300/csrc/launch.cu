@@ -51,6 +51,14 @@ void launch_bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot,
                          int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom) {
     AFG_BY_DIM(bottom_block, c, A, nroot, bct, root_box, N, mode, u, rho, vold, nd, nu, nb, hom);
 }
+size_t bottom_block_smem(int D, bool fp64, int N, const int *nroot, const int *bct) {
+    BlockTree B;
+    for (int a = 0; a < 3; ++a) B.nroot[a] = a < D ? nroot[a] : 1;
+    for (int s = 0; s < 6; ++s) B.bct[s] = s < 2 * D ? bct[s] : 0;
+    B.root_box = nullptr;
+    if (D == 2) return fp64 ? block_bottom_smem<2, double>(N, B) : block_bottom_smem<2, float>(N, B);
+    return fp64 ? block_bottom_smem<3, double>(N, B) : block_bottom_smem<3, float>(N, B);
+}
 void launch_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *u, const void *rho,
                    const void *rhoh, double h2, int colour, int hom) {
     AFG_BY_DIM(smooth, c, A, b0, n, list, u, rho, rhoh, h2, colour, hom);

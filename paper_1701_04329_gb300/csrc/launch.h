@@ -31,6 +31,8 @@ void launch_bottom(const LaunchCfg &, const BoxMeta &, int ntrees, int N, int lm
 // the block's grids do not fit one CTA's shared memory.
 void launch_bottom_block(const LaunchCfg &, const BoxMeta &, const int *nroot, const int *bct, const int *root_box,
                          int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom);
+// shared memory that launch needs (bytes)
+size_t bottom_block_smem(int D, bool fp64, int N, const int *nroot, const int *bct);
 // rhoh (may be null): use the pre-scaled source -h^2 rho/(2D) instead of rho
 void launch_smooth(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u, const void *rho,
                    const void *rhoh, double h2, int colour, int hom);
