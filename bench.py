@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -49,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default="twosrc3d", choices=["twosrc3d", "gauss2d", "blobs3d"],
                     help="problem of the --solve-only mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="only the headline workload (profiling runs)")
     ap.add_argument("--kernel-only", choices=["smooth", "resid", "correct", "leafres"],
                     help="time one kernel on a uniform tree of --uniform-level (profiling case)")
     ap.add_argument("--solve-only", choices=["fp64", "mixed"],
@@ -72,35 +75,9 @@ def forest_mode(args):
 
 
 def paper_cmp(args):
-    """The paper's Sec. 4.2 problem: Laplacian(phi) = 1, phi = 0 on [0,1]^3,
-    uniform 512^3 (1.34e8 unknowns), boxes 8^3, one FMG cycle with (2,2,4)."""
+    """Only the paper-comparison workload (uniform 512^3, one FMG)."""
     import torch
-    from paper_1701_04329_gb300 import afgpu
-    from paper_1701_04329_gb300 import workloads as W
-    p = W.uniform3d(level=7)
-    t = afgpu.Tree(3, 8, 7)
-    t.refine_uniform(7)
-    n = t.n_leaf_cells
-    t.set_rhs(torch.ones(n, dtype=torch.float64, device="cuda"))
-    zero = torch.zeros(n, dtype=torch.float64, device="cuda")
-    out = {"workload": "uniform 512^3, Laplacian(phi)=1, phi=0, 8^3 boxes, one FMG (2,2,4)", "unknowns": n}
-    for name, prec in (("fp64", afgpu.AFG_FP64), ("mixed", afgpu.AFG_MIXED)):
-        opts = afgpu.default_opts(precision=prec, rel_tol=0.0, max_cycles=1)
-        ms = []
-        for i in range(args.warmup + args.steps):
-            t.set_solution(zero)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            if prec == afgpu.AFG_FP64:
-                st = t.fmg(opts)
-            else:
-                st = t.solve(opts, allow_not_converged=True)
-            torch.cuda.synchronize()
-            if i >= args.warmup:
-                ms.append((time.perf_counter() - t0) * 1e3)
-        out[name] = {"ms_per_fmg": min(ms), "ns_per_unknown": min(ms) * 1e6 / n, "rel_residual": st["rel_residual"]}
-    out["paper_ns_per_unknown_8cubed_16_cores"] = 22.0
-    print(json.dumps(out), flush=True)
+    print(json.dumps(bench_paper_cmp(args.steps, args.warmup, torch.device("cuda"))), flush=True)
 
 
 def solve_only(args):
@@ -273,8 +250,10 @@ def twin_errors(tree, uniform_level, dev, opts):
     return res
 
 
-def cpu_baseline(problem, tol, steps=1):
-    """The oracle as it stands, on this host's cores: full solves to `tol`."""
+def cpu_baseline(problem, tol, steps=1, ref_tol=1e-12):
+    """The oracle as it stands, on this host's cores: full solves to `tol`
+    (timed), then V-cycles on to `ref_tol` (untimed), whose solution is the
+    reference of the error report."""
     from oracle.oracle import OracleTree
     t = OracleTree(problem.dim, problem.box_n, problem.max_level)
     problem.build(t)
@@ -287,8 +266,198 @@ def cpu_baseline(problem, tol, steps=1):
         t0 = time.perf_counter()
         cycles = t.solve(tol, 60)
         times.append(time.perf_counter() - t0)
+    for _ in range(30):  # on to the FP64 floor, untimed
+        r, pm = t.residual_norm()
+        if r <= ref_tol * pm:
+            break
+        t.vcycle()
+    r, pm = t.residual_norm()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return t.n_leaf_cells, times, cycles, cores
+    return dict(cells=t.n_leaf_cells, times=times, cycles=cycles, cores=cores, u_ref=t.get_solution(),
+                ref_rel_residual=r / pm)
+
+
+def oracle_reference(problem, ref_tol=1e-12):
+    """The oracle's FP64 solution of a (small) workload taken to `ref_tol`
+    (untimed; the reference of an error report)."""
+    from oracle.oracle import OracleTree
+    t = OracleTree(problem.dim, problem.box_n, problem.max_level)
+    problem.build(t)
+    rho, b = problem.data(t)
+    t.set_rhs(rho)
+    t.set_dirichlet(b)
+    t.zero_solution()
+    t.solve(ref_tol, 80)
+    return t.get_solution()
+
+
+def rel_err(u, ref):
+    import numpy as np
+    u = u.cpu().numpy() if hasattr(u, "cpu") else u
+    return float(np.abs(u - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def event_time(fn, K, W_, stream_sync=True):
+    """Mean ms of fn() over K calls after W_ warm-up calls (CUDA events on the
+    current stream, synchronised on both sides)."""
+    import torch
+    out = None
+    for _ in range(W_):
+        out = fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K, out
+
+
+def bench_gauss2d(K, W_, dev, with_oracle):
+    """configs[0]-style 2D workload: one Gaussian, 8^2 boxes, levels 4..7;
+    time to 1e-8 and to 1e-10 (FP64 and mixed), graph replay on and off,
+    error against the exact u and against the oracle's FP64 solution."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    from paper_1701_04329_gb300 import workloads as W
+    p = W.gauss2d()
+    t = afgpu.Tree(p.dim, p.box_n, p.max_level)
+    p.build(t)
+    rho_h, b_h = p.data(t)
+    rho, bv = torch.tensor(rho_h, device=dev), torch.tensor(b_h, device=dev)
+    zero = torch.zeros_like(rho)
+    ue = torch.tensor(p.u_exact(t.cell_centers()), device=dev)
+    t.set_rhs(rho)
+    t.set_dirichlet(bv)
+    ref = oracle_reference(p) if with_oracle else None
+    out = {"workload": "2D quadtree, boxes 8^2, uniform 64^2 (level 4) refined to level 7 where |rho| h^2 > 1e-4 "
+                       "around u = exp(-|x-(.5,.5)|^2/0.04^2), Dirichlet b = u; FMG + V(2,2)",
+           "unknowns": t.n_leaf_cells, "unit": "ms per solve"}
+    for name, prec in (("fp64", afgpu.AFG_FP64), ("mixed", afgpu.AFG_MIXED)):
+        row = {}
+        for tol in (1e-8, 1e-10):
+            for graph in (1, 0):
+                opts = afgpu.default_opts(rel_tol=tol, precision=prec, use_graph=graph)
+
+                def step():
+                    t.set_solution(zero)
+                    return t.solve(opts)
+                ms, st = event_time(step, K, W_)
+                key = "ms_to_%g" % tol + ("" if graph else "_graph_off")
+                row[key] = ms
+                if graph:
+                    row["cycles_to_%g" % tol] = st["cycles"]
+        u = t.get_solution()
+        row["max_err_vs_exact_rel"] = float((u - ue).abs().max() / ue.abs().max())
+        row["err_vs_oracle"] = rel_err(u, ref) if ref is not None else None
+        row["unknowns_per_s_to_1e-10"] = t.n_leaf_cells / (row["ms_to_1e-10"] * 1e-3)
+        out[name] = row
+    return out
+
+
+def bench_blobs3d(K, W_, dev):
+    """configs[4]-style differentiable 3D workload (uniform 128^3 + 1 level,
+    8 Gaussian blobs): the forward solve and the backward (adjoint) solve
+    through torch.autograd, to 1e-10 each."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    from paper_1701_04329_gb300 import workloads as W
+    from paper_1701_04329_gb300.autograd import PoissonSolve
+    p = W.blobs3d()
+    t = afgpu.Tree(p.dim, p.box_n, p.max_level)
+    p.build(t)
+    rho_h, b_h = p.data(t)
+    x = t.cell_centers()
+    ustar = torch.tensor(1e-4 * W.blobs3d(seed=2).rho(x), device=dev)
+    h = torch.tensor(1.0 / (8 * 2.0 ** (np.repeat(t.leaf_levels(), 512) - 1)), device=dev)
+    vol = h ** 3
+    opts = afgpu.default_opts(rel_tol=1e-10)
+    rho = torch.tensor(rho_h, device=dev, requires_grad=True)
+    b = torch.tensor(b_h, device=dev, requires_grad=True)
+    fwd, bwd = [], []
+    for i in range(W_ + K):
+        rho.grad = None
+        b.grad = None
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record()
+        u = PoissonSolve.apply(rho, b, t, opts, opts)
+        loss = 0.5 * (vol * (u - ustar) ** 2).sum()
+        e[1].record()
+        loss.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if i >= W_:
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+    f, bk = sum(fwd) / K, sum(bwd) / K
+    return {"workload": "3D octree, boxes 8^3, uniform 128^3 + 1 level where |rho| > 0.1 max|rho|, 8 Gaussian blobs "
+                        "(s=0.03); loss = 0.5 sum vol (u - u*)^2; forward solve and adjoint solve to 1e-10",
+            "unknowns": t.n_leaf_cells, "forward_ms": f, "backward_ms": bk, "fwd_bwd_ms": f + bk,
+            "unit": "ms per forward+backward", "grad_norm_rho": float(rho.grad.abs().max())}
+
+
+def bench_paper_cmp(K, W_, dev):
+    """The paper's Sec. 4.2 problem: Laplacian(phi) = 1, phi = 0 on [0,1]^3,
+    uniform 512^3 (1.34e8 unknowns), boxes 8^3, one FMG cycle with (2,2,4)."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu
+    t = afgpu.Tree(3, 8, 7)
+    t.refine_uniform(7)
+    n = t.n_leaf_cells
+    t.set_rhs(torch.ones(n, dtype=torch.float64, device=dev))
+    zero = torch.zeros(n, dtype=torch.float64, device=dev)
+    out = {"workload": "uniform 512^3, Laplacian(phi)=1, phi=0, 8^3 boxes, one FMG (2,2,4)", "unknowns": n,
+           "paper_ns_per_unknown": 22.0, "paper_hardware": "Xeon E5-2680, 16 OpenMP threads (context)"}
+    for name, prec in (("fp64", afgpu.AFG_FP64), ("mixed", afgpu.AFG_MIXED)):
+        opts = afgpu.default_opts(precision=prec, rel_tol=0.0, max_cycles=1)
+
+        def step():
+            t.set_solution(zero)
+            return t.fmg(opts) if prec == afgpu.AFG_FP64 else t.solve(opts, allow_not_converged=True)
+        ms, st = event_time(step, K, W_)
+        out[name] = {"ms_per_fmg": ms, "ns_per_unknown": ms * 1e6 / n, "rel_residual": st["rel_residual"]}
+    t.close()
+    return out
+
+
+def bench_forest(K, W_, dev, hbm):
+    """configs[3]-style batched workload at the tuner's recorded choice: 512
+    quadtrees (seeds 1000+t), mixed precision to 1e-8 per tree, CUDA-graph
+    replay; unknowns/s and the roofline of its FP32 half-sweep."""
+    import torch
+    from paper_1701_04329_gb300 import afgpu, autotune
+    choice = autotune.tuned_choice()
+    box_n, nd, nu = choice or (16, 2, 2)
+    trees, rho_h, b_h = autotune.build_forest(512, box_n)
+    f = afgpu.Forest(trees)
+    f.set_rhs(torch.tensor(rho_h, device=dev))
+    f.set_dirichlet(torch.tensor(b_h, device=dev))
+    n = int(f.cells.sum())
+    opts = afgpu.default_opts(rel_tol=1e-8, precision=afgpu.AFG_MIXED, n_down=nd, n_up=nu, max_cycles=60)
+    l0 = afgpu.kernel_launches()
+    ms, st = event_time(lambda: f.solve(opts), K, W_)
+    launches = (afgpu.kernel_launches() - l0) // (K + W_)
+    lv = [tr.info() for tr in trees]
+    top = max(i.highest_level for i in lv)
+    boxes = [sum(i.boxes_per_level[l] for i in lv) for l in range(top + 1)]
+    lvl = max(range(1, top + 1), key=lambda l: boxes[l])
+    k32 = f.time_kernel(0, lvl, False, 20)
+    gbs = k32["bytes"] / (k32["ms"] * 1e-3) / 1e9
+    out = {"workload": "512 2D quadtrees (seeds 1000+t), 1-4 Gaussian sources, max level 4..9 (8^2 boxes; one "
+                       "fewer with 16^2), mixed precision to 1e-8 per tree, CUDA graph",
+           "config": {"box_n": box_n, "n_down": nd, "n_up": nu, "source": "tuned_forest.json" if choice else "default"},
+           "value": n / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "unknowns": n,
+           "max_cycles": max(s["cycles"] for s in st), "worst_rel_residual": max(s["rel_residual"] for s in st),
+           "gpu_launches_per_step": launches,
+           "roofline": {"bound": "hbm", "kernel": "k_smooth_p<2,%d,float> (half-sweep, level %d, all trees)" % (box_n, lvl),
+                        "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "ms": k32["ms"],
+                        "algorithmic_bytes": k32["bytes"], "traffic": None}}
+    f.close()
+    for tr in trees:
+        tr.close()
+    return out
 
 
 def run_reference(args):
@@ -402,14 +571,7 @@ def main():
     u64 = u.clone()
     msmx, stmx, launches_mx = timed(make_step(optsmx), args.steps, args.warmup)
     umx = u.clone()
-    # reference solution for the error report: FP64 to 1e-12 (parity-tested against the oracle)
-    tree.set_solution(zero)
-    tree.solve(afgpu.default_opts(rel_tol=1e-12), allow_not_converged=True)
-    uref = tree.get_solution()
-    scale = float(uref.abs().max())
-    err64 = float((u64 - uref).abs().max()) / scale
-    errmx = float((umx - uref).abs().max()) / scale
-
+    # error report against the oracle's FP64 solution (the cpu_baseline leg below)
     # end to end through the public API with host buffers (pinned), copies timed
     rho_pin = torch.tensor(rho_h).pin_memory()
     b_pin = torch.tensor(b_h).pin_memory()
@@ -461,7 +623,7 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": n, "boxes": info.n_boxes, "highest_level": info.highest_level,
                    "cycles": st64["cycles"], "rel_residual": st64["rel_residual"],
-                   "err_vs_fp64_1e-12": err64, "l2": "working set > L2 (no flush needed)",
+                   "err_vs_oracle": None, "l2": "working set > L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "k_smooth_p<3,8,double> (half-sweep, level %d)" % lvl,
                      "arithmetic": "per update 7 FP64-equivalent flops: the x and y neighbours summed exactly "
@@ -473,7 +635,7 @@ def main():
                      "traffic": TRAFFIC.get(("k_smooth_p<3,8,double>", lvl)), "traffic_unit": TRAFFIC_UNIT,
                      "algorithmic_bytes": k64["bytes"]},
         "mixed": {"value": vmx, "unit": "unknowns/s", "ms_per_step": msmx, "dtype": "f32+f64",
-                  "cycles": stmx["cycles"], "rel_residual": stmx["rel_residual"], "err_vs_fp64_1e-12": errmx,
+                  "cycles": stmx["cycles"], "rel_residual": stmx["rel_residual"], "err_vs_oracle": None,
                   "speedup_vs_fp64": ms64 / msmx, "gpu_launches": launches_mx,
                   "e2e": {"value": world * n / (ms_e2e_mx * 1e-3), "unit": "unknowns/s"},
                   "roofline": {"bound": "hbm", "kernel": "k_smooth_p<3,8,float> (half-sweep, level %d)" % lvl,
@@ -487,11 +649,30 @@ def main():
         "clocks": clk,
         "manufactured_twin": twin,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nc, times, cyc, cores = cpu_baseline(p, args.tol)
-        out["cpu_baseline"] = {"value": nc / min(times), "unit": "unknowns/s", "cores": cores, "kind": "oracle",
-                               "sample": "one full FP64 solve of the same workload to rel. residual %g (%d cycles, %.1f s)"
-                                         % (args.tol, cyc, min(times))}
+    # the other workloads, each timed on this GPU (a failure only loses its entry)
+    with_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
+    K2 = max(1, min(args.steps, 5))
+    extra = (("gauss2d", lambda: bench_gauss2d(K2, args.warmup, dev, with_oracle)),
+             ("blobs3d_fwd_bwd", lambda: bench_blobs3d(K2, max(1, min(args.warmup, 2)), dev)),
+             ("paper_cmp", lambda: bench_paper_cmp(K2, args.warmup, dev)),
+             ("forest", lambda: bench_forest(K2, args.warmup, dev, hbm)))
+    for key, fn in extra:
+        if args.skip_extra or world > 1:  # replicas time the headline workload only
+            break
+        try:
+            out[key] = fn()
+        except Exception as ex:  # noqa: BLE001 - reported in the JSON line instead
+            out[key] = {"error": str(ex)[:300]}
+        torch.cuda.synchronize()
+    if with_oracle:
+        cb = cpu_baseline(p, args.tol)
+        out["cpu_baseline"] = {"value": cb["cells"] / min(cb["times"]), "unit": "unknowns/s", "cores": cb["cores"],
+                               "kind": "oracle",
+                               "sample": "one full FP64 solve of the same workload to rel. residual %g (%d cycles, "
+                                         "%.1f s)" % (args.tol, cb["cycles"], min(cb["times"]))}
+        out["config"]["err_vs_oracle"] = rel_err(u64, cb["u_ref"])
+        out["mixed"]["err_vs_oracle"] = rel_err(umx, cb["u_ref"])
+        out["config"]["oracle_ref_rel_residual"] = cb["ref_rel_residual"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

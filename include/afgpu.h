@@ -24,6 +24,13 @@
  *   They are enqueued on the handle's stream (afg_set_stream, default the
  *   legacy default stream) and the pointers must stay valid until that work
  *   has finished.  Calls returning host values (norms, stats) synchronise.
+ * - A handle's device data lives on one CUDA device: for a tree, the device
+ *   current at its first field call; for a forest, the device current at
+ *   afg_forest_create.  Every later call on the handle runs on that device
+ *   (the library makes it current for the call and restores the caller's
+ *   device on return), so pointers and streams given to it must belong to it.
+ * - Device memory of the library (tree metadata, field workspaces) comes from
+ *   cudaMalloc, or from the caller's allocator (afg_set_allocator).
  * - Leaf data order ("canonical"): leaf boxes by level ascending, Morton
  *   order (x lowest bit) of the spatial index within a level; cells of a box
  *   lexicographic with x fastest.  Boundary faces: leaf boxes in the same
@@ -94,6 +101,22 @@ void afg_default_opts(afg_mg_opts *opts);
 
 const char *afg_last_error(void);
 
+/* Device memory allocator for every buffer the library allocates from now on
+ * (the paper's code allocates per box on the host; this is the GPU
+ * counterpart: a framework such as PyTorch passes its caching allocator so
+ * that the solver's workspaces come out of its pool).  alloc(bytes, ctx)
+ * returns device memory of the current device, 256-byte aligned, or NULL
+ * (the library call then fails with AFG_ERR_NOMEM); dealloc(ptr, ctx) takes
+ * back a pointer alloc returned, with the same device current.  A buffer is
+ * always returned to the allocator that made it, also after a later
+ * afg_set_allocator; before calling dealloc the library waits for the device
+ * to finish its queued work (as cudaFree does), so the memory may be reused
+ * at once.  Both NULL: back to cudaMalloc/cudaFree.  One of them NULL:
+ * AFG_ERR_ARG.  Process-wide and not synchronised with other threads: set it
+ * before creating handles.  Pinned host buffers (a few bytes per handle for
+ * norms read back) still come from cudaMallocHost. */
+int afg_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*dealloc)(void *ptr, void *ctx), void *ctx);
+
 /* ---- tree (Sec. 2.1-2.3) ------------------------------------------------ */
 
 /* Create a tree on [0,1]^dim with one root box of box_n^dim cells (level 1).
@@ -106,10 +129,15 @@ int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out);
  * the domain is [0,nroot[0]] x [0,nroot[1]] (x [0,nroot[2]]).  Root boxes
  * come first in the canonical box order (Morton order of their indices).
  * Every call accepts such trees: below level 1 the coarse grids hold one box
- * per root, solved together in one CTA (Sec. 3.2), which takes up to about
- * 16 roots of 8^3 boxes in 3D FP64 (larger blocks fail with AFG_ERR_STATE at
- * the first multigrid call); forests of them are refused (AFG_ERR_STATE).
- * AFG_ERR_ARG when nroot[a] << (max_level-1) exceeds 2^21. */
+ * per root, solved together in one CTA (Sec. 3.2), so level 1 and those
+ * grids must fit one CTA's shared memory (227 KB on GB300): per grid of M =
+ * 2, 4, ..., N cells per root, 4 FP64 arrays of (r_x M + 2)(r_y M + 2)
+ * (x (r_z M + 2)) values plus the face data of the non-periodic sides.  That takes up to 8 x 8 roots of 8^2 boxes (2D), 4 x 4
+ * of 16^2 boxes, 6 x 1 x 1 or 3 x 2 x 1 roots of 8^3 boxes (a 2 x 2 x 2 block
+ * of 8^3 boxes is refused) and no block of 16^3 boxes.  A larger block fails
+ * with AFG_ERR_STATE at its first field call (afg_set_rhs and the like), when
+ * the device grid is built.  Forests of such trees, of any size, are refused
+ * (AFG_ERR_STATE).  AFG_ERR_ARG when nroot[a] << (max_level-1) exceeds 2^21. */
 int afg_tree_create_roots(int dim, int box_n, int max_level, const int *nroot, afg_tree **out);
 int afg_tree_destroy(afg_tree *t);
 
@@ -121,6 +149,10 @@ int afg_refine_uniform(afg_tree *t, int level);
 
 /* Leaf cell centres, canonical order, dim doubles per cell (host memory). */
 int afg_cell_centers(const afg_tree *t, double *xyz_host);
+
+/* The same leaf cell centres written into device memory (dim doubles per
+ * leaf cell, n_leaf_cells * dim in all) by a kernel on the tree's stream. */
+int afg_cell_centers_device(afg_tree *t, double *xyz_dev);
 
 /* Centres of the leaf boundary faces, canonical face order (host memory). */
 int afg_face_centers(const afg_tree *t, double *xyz_host);
@@ -220,6 +252,28 @@ int afg_forest_get_solution(const afg_forest *f, double *u_dev);
  * later cycles.  per_tree (may be NULL) receives n stats records. */
 int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree);
 
+/* Autotuner for batched forests (an addition to the paper's method, whose
+ * runs fix the box size and N_down = N_up = 2).  candidates[n]: forests of
+ * the same problems built with different box sizes (8^2 and 16^2 cells, the
+ * finest spacing equal), each with its source term and boundary data set.
+ * json_in (may be NULL): {"sweeps": [[n_down, n_up], ...], "reps": R},
+ * default sweeps [[1,1],[2,2],[3,3]] and R = 3.  For every candidate and
+ * pair it runs afg_forest_solve with `base` (NULL: mixed precision to 1e-8)
+ * and that pair -- one warm-up solve, which also captures the CUDA graphs,
+ * then the fastest of R solves timed with CUDA events on the forest's
+ * stream -- and writes to json_out (cap bytes, NUL-terminated) the report
+ * {"objective": "unknowns_per_s", "best": ROW, "table": [ROW, ...]}, ROW =
+ * {"candidate", "box_n", "n_down", "n_up", "ms", "unknowns",
+ * "unknowns_per_s", "converged", "worst_rel_residual", "max_cycles"}.  The
+ * best row is the converged one with the most unknowns per second: time to
+ * the tolerance per unknown, which compares the box sizes' different meshes
+ * per unknown.  Threads per box are not a knob: every kernel gives one
+ * thread to each 16-byte vector of a box's colour half, which the box size
+ * fixes.  AFG_ERR_ARG on a malformed json_in or a too small json_out (the
+ * message gives the size needed).  Each forest's solution is overwritten. */
+int afg_autotune(afg_forest *const *candidates, int n, const afg_mg_opts *base, const char *json_in,
+                 char *json_out, size_t cap);
+
 /* Allocation-free residual norms of a forest.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * where they check convergence -- e.g. a host framework that has handed the
@@ -266,6 +320,10 @@ int afg_kernel_launches(unsigned long long *count);
  * are overwritten.  Needs afg_set_rhs first. */
 int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
                     double *flops, long long *cells);
+/* The same timing on a forest: the launches cover the level's boxes of all
+ * its trees (the concatenated box list of that level). */
+int afg_forest_time_kernel(afg_forest *f, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
+                           double *flops, long long *cells);
 
 #ifdef __cplusplus
 }

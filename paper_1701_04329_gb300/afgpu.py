@@ -67,7 +67,45 @@ _SIGS = {
     "afg_forest_solve": (I, [P, P, P]), "afg_kernel_launches": (I, [P]),
     "afg_time_kernel": (I, [P, I, I, I, I, P, P, P, P]),
     "afg_forest_residual_norms_noalloc": (I, [P, P, P]),
+    "afg_set_allocator": (I, [P, P, P]), "afg_cell_centers_device": (I, [P, P]),
+    "afg_forest_time_kernel": (I, [P, I, I, I, I, P, P, P, P]),
+    "afg_autotune": (I, [P, I, P, ctypes.c_char_p, P, ctypes.c_size_t]),
 }
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEALLOC_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+# every callback pair ever installed: a buffer goes back to the callbacks that
+# made it, so none of them may be freed while the process runs
+_ALLOCATORS = []
+
+
+def set_allocator(alloc, dealloc):
+    """Route the library's device allocations through alloc(nbytes) -> int
+    pointer and dealloc(pointer) (afg_set_allocator); both None restores
+    cudaMalloc.  Set it before creating trees and forests."""
+    if alloc is None and dealloc is None:
+        _check(lib().afg_set_allocator(None, None, None))
+        return
+
+    def a(n, _ctx):
+        try:
+            return int(alloc(int(n)))
+        except Exception:  # noqa: BLE001 - the library reports NULL as AFG_ERR_NOMEM
+            return None
+
+    def d(ptr, _ctx):
+        dealloc(int(ptr))
+
+    cbs = (ALLOC_FN(a), DEALLOC_FN(d))
+    _ALLOCATORS.append(cbs)
+    _check(lib().afg_set_allocator(ctypes.cast(cbs[0], P), ctypes.cast(cbs[1], P), None))
+
+
+def use_torch_allocator():
+    """Take the library's device memory from PyTorch's caching allocator (on
+    the stream current at each allocation)."""
+    import torch
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n), torch.cuda.caching_allocator_delete)
 
 
 def kernel_launches():
@@ -186,6 +224,17 @@ class Tree:
         x = np.zeros((self.n_leaf_cells, self.D))
         _check(lib().afg_cell_centers(self._h, x.ctypes.data_as(P)))
         return x
+
+    def cell_centers_device(self, out=None):
+        """Leaf cell centres as a (n_leaf_cells, dim) float64 CUDA tensor,
+        written by the library's kernel."""
+        import torch
+        self._sync_stream()
+        n = self.n_leaf_cells
+        if out is None:
+            out = torch.empty((n, self.D), dtype=torch.float64, device="cuda")
+        _check(lib().afg_cell_centers_device(self._h, _dev(out.view(-1), n * self.D)))
+        return out
 
     def face_centers(self):
         x = np.zeros((self.n_bfaces, self.D))
@@ -342,6 +391,15 @@ class Forest:
         p = np.zeros(self.T)
         _check(lib().afg_forest_residual_norms_noalloc(self._h, r.ctypes.data_as(P), p.ctypes.data_as(P)))
         return r, p
+
+    def time_kernel(self, kernel, level, fp64=True, reps=20):
+        """afg_forest_time_kernel: mean ms of one launch over the level's boxes
+        of every tree, with its algorithmic bytes, flops and cells."""
+        self._sync_stream()
+        ms, by, fl, nc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        _check(lib().afg_forest_time_kernel(self._h, kernel, level, int(fp64), reps, ctypes.byref(ms),
+                                            ctypes.byref(by), ctypes.byref(fl), ctypes.byref(nc)))
+        return dict(ms=ms.value, bytes=by.value, flops=fl.value, cells=nc.value)
 
     def solve(self, opts=None, allow_not_converged=False):
         self._sync_stream()

@@ -2,19 +2,28 @@
 
 For a workload of independent 2D quadtrees it builds the forest with boxes
 of 8^2 and of 16^2 cells (one level fewer with 16^2, so the finest spacing
-is the same), and for each box size times the solve to the tolerance with
-every candidate pair of smoothing steps (N_down, N_up); the fastest
-configuration wins.  Threads per box are not a free knob here: every kernel
-assigns one thread per 16-byte vector of a box's colour half (or per cell
-pair for small boxes), so the box size fixes them; the tuner reports them.
-Timing: CUDA events around whole solves, after one warm-up solve.
+is the same) and hands both to the library's tuner (``afg_autotune``), which
+times the solve to the tolerance for every pair of smoothing steps (N_down,
+N_up) and picks the configuration with the most unknowns per second (time
+to the tolerance per unknown: the two box sizes refine to different meshes
+at the same finest spacing).  Threads per box are not a free knob: every
+kernel gives one thread to each 16-byte vector of a box's colour half, so
+the box size fixes them; the tuner reports them.
+
+``python -m paper_1701_04329_gb300.autotune 512`` on a GPU writes the choice
+to ``tuned_forest.json`` beside this file; ``bench.py`` times the batched
+workload at that configuration.
 """
+import ctypes
 import json
+import os
 
 import numpy as np
 
 from . import afgpu
 from . import workloads as W
+
+TUNED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_forest.json")
 
 
 def build_forest(n_trees, box_n, seed0=1000, max_level_cap=None):
@@ -38,51 +47,59 @@ def threads_per_box(dim, box_n, fp32=True):
     return min(max(half // vec, 1), 256)
 
 
-def time_forest(forest, rho, b, opts, reps=3):
-    import torch
-    f_rho = torch.tensor(rho, device="cuda")
-    f_b = torch.tensor(b, device="cuda")
-    forest.set_rhs(f_rho)
-    forest.set_dirichlet(f_b)
-    stats = forest.solve(opts, allow_not_converged=True)  # warm-up (builds the CUDA graphs)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms = []
-    for _ in range(reps):
-        torch.cuda.synchronize()
-        ev0.record()
-        stats = forest.solve(opts, allow_not_converged=True)
-        ev1.record()
-        torch.cuda.synchronize()
-        ms.append(ev0.elapsed_time(ev1))
-    worst = max(s["rel_residual"] for s in stats)
-    return min(ms), worst, stats
-
-
 def autotune_forest(n_trees=512, seed0=1000, tol=1e-8, precision=afgpu.AFG_MIXED, box_sizes=(8, 16),
                     sweeps=((1, 1), (2, 2), (3, 3)), reps=3, max_level_cap=None):
-    """Returns (best, table): best is a dict of the chosen configuration."""
-    table = []
+    """Returns (best, table) from afg_autotune, rows extended with the
+    threads per box."""
+    import torch
+    forests, keep = [], []
     for box_n in box_sizes:
         trees, rho, b = build_forest(n_trees, box_n, seed0, max_level_cap)
-        forest = afgpu.Forest(trees)
-        cells = int(forest.cells.sum())
-        for nd, nu in sweeps:
-            opts = afgpu.default_opts(rel_tol=tol, precision=precision, n_down=nd, n_up=nu, max_cycles=60)
-            ms, worst, stats = time_forest(forest, rho, b, opts, reps)
-            table.append(dict(box_n=box_n, n_down=nd, n_up=nu, threads_per_box=threads_per_box(2, box_n),
-                              ms=ms, unknowns=cells, unknowns_per_s=cells / (ms * 1e-3),
-                              converged=bool(worst <= tol), worst_rel_residual=worst,
-                              max_cycles=max(s["cycles"] for s in stats)))
-        forest.close()
+        f = afgpu.Forest(trees)
+        f.set_rhs(torch.tensor(rho, device="cuda"))
+        f.set_dirichlet(torch.tensor(b, device="cuda"))
+        forests.append(f)
+        keep.append(trees)
+    base = afgpu.default_opts(rel_tol=tol, precision=precision, max_cycles=60)
+    spec = json.dumps({"sweeps": [list(s) for s in sweeps], "reps": reps}).encode()
+    out = ctypes.create_string_buffer(1 << 16)
+    arr = (ctypes.c_void_p * len(forests))(*[f._h.value for f in forests])
+    for f in forests:
+        f._sync_stream()
+    afgpu._check(afgpu.lib().afg_autotune(arr, len(forests), ctypes.byref(base), spec, out, len(out)))
+    rep = json.loads(out.value.decode())
+    for r in rep["table"] + [rep["best"]]:
+        r["threads_per_box"] = threads_per_box(2, r["box_n"])
+    for f in forests:
+        f.close()
+    for trees in keep:
         for t in trees:
             t.close()
-    ok = [r for r in table if r["converged"]] or table
-    best = min(ok, key=lambda r: r["ms"])
-    return best, table
+    return rep["best"], rep["table"]
+
+
+def record(best, table, n_trees, tol, path=TUNED):
+    with open(path, "w") as f:
+        json.dump({"workload": "batched 2D forest, %d trees, seeds 1000+t" % n_trees, "tol": tol,
+                   "objective": "unknowns_per_s", "best": best, "table": table}, f, indent=1)
+        f.write("\n")
+
+
+def tuned_choice(path=TUNED):
+    """The recorded choice (box_n, n_down, n_up), or None."""
+    try:
+        with open(path) as f:
+            b = json.load(f)["best"]
+        return int(b["box_n"]), int(b["n_down"]), int(b["n_up"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 if __name__ == "__main__":
     import sys
     n = int(sys.argv[1]) if len(sys.argv) > 1 else 64
-    best, table = autotune_forest(n)
+    tol = 1e-8
+    best, table = autotune_forest(n, tol=tol)
+    if n == 512:
+        record(best, table, n, tol)
     print(json.dumps({"best": best, "table": table}, indent=1))

@@ -26,6 +26,9 @@ int fail(int code, const std::string &msg) {
 }
 
 #define AFG_API_BEGIN try {
+// inside AFG_API_BEGIN: run the rest of the call on the handle's device
+#define AFG_ON_DEVICE(h) afg::DeviceGuard afg_device_guard_((h)->device_for_call())
+#define AFG_ON_FOREST_DEVICE(f) afg::DeviceGuard afg_device_guard_((f)->device)
 #define AFG_API_END                                                      \
     }                                                                    \
     catch (const afg::NoMem &e) { return fail(AFG_ERR_NOMEM, e.what()); } \
@@ -350,6 +353,15 @@ void afg_default_opts(afg_mg_opts *o) {
 
 const char *afg_last_error(void) { return g_err.c_str(); }
 
+int afg_set_allocator(void *(*alloc)(size_t, void *), void (*dealloc)(void *, void *), void *ctx) {
+    if ((alloc == nullptr) != (dealloc == nullptr)) return fail(AFG_ERR_ARG, "give both callbacks or neither");
+    afg::Allocator &a = afg::allocator();
+    a.alloc = alloc;
+    a.dealloc = dealloc;
+    a.ctx = alloc ? ctx : nullptr;
+    return AFG_OK;
+}
+
 int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out) {
     if (!out) return fail(AFG_ERR_ARG, "out is NULL");
     if (dim != 2 && dim != 3) return fail(AFG_ERR_ARG, "dim must be 2 or 3");
@@ -410,6 +422,16 @@ int afg_cell_centers(const afg_tree *t, double *xyz) {
         }
     }
     return AFG_OK;
+}
+
+int afg_cell_centers_device(afg_tree *t, double *xyz_dev) {
+    if (!t || !xyz_dev) return fail(AFG_ERR_ARG, "null argument");
+    AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
+    Grid &g = grid_of(t);
+    afg::launch_cell_centers(g, xyz_dev, t->stream);
+    return AFG_OK;
+    AFG_API_END
 }
 
 int afg_face_centers(const afg_tree *t, double *xyz) {
@@ -506,6 +528,7 @@ int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *pa
 int afg_set_rhs(afg_tree *t, const double *rho) {
     if (!t || !rho) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     afg::launch_leaf_set(g.leaf_cfg(true, t->stream), g.meta, g.d_leaves, g.n_leaf_boxes, rho, g.ws64.rho->p);
     g.leaf_rho_hat(g.ws64, t->stream);
@@ -518,6 +541,7 @@ int afg_set_rhs(afg_tree *t, const double *rho) {
 int afg_set_dirichlet(afg_tree *t, const double *b) {
     if (!t || !b) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     set_dirichlet_dev(g, b, t->stream);
     check(cudaGetLastError(), "afg_set_dirichlet");
@@ -528,6 +552,7 @@ int afg_set_dirichlet(afg_tree *t, const double *b) {
 int afg_set_solution(afg_tree *t, const double *u) {
     if (!t || !u) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     afg::launch_leaf_set(g.leaf_cfg(true, t->stream), g.meta, g.d_leaves, g.n_leaf_boxes, u, g.ws64.u->p);
     check(cudaGetLastError(), "afg_set_solution");
@@ -539,6 +564,7 @@ int afg_get_solution(const afg_tree *tc, double *u) {
     afg_tree *t = const_cast<afg_tree *>(tc);
     if (!t || !u) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     afg::launch_leaf_get(g.leaf_cfg(true, t->stream), g.meta, g.d_leaves, g.n_leaf_boxes, g.ws64.u->p, u);
     check(cudaGetLastError(), "afg_get_solution");
@@ -551,6 +577,7 @@ static int one_cycle(afg_tree *t, const afg_mg_opts *opts, afg_stats *st, bool f
     const afg_mg_opts o = opts_or_default(opts);
     if (int rc = validate(o)) return rc;
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
     const auto t0 = clk::now();
@@ -578,6 +605,7 @@ int afg_solve(afg_tree *t, const afg_mg_opts *opts, afg_stats *st) {
     const afg_mg_opts o = opts_or_default(opts);
     if (int rc = validate(o)) return rc;
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
     const auto t0 = clk::now();
@@ -598,6 +626,7 @@ int afg_solve(afg_tree *t, const afg_mg_opts *opts, afg_stats *st) {
 int afg_residual_norm(afg_tree *t, double *max_abs_r, double *max_abs_rho) {
     if (!t) return fail(AFG_ERR_ARG, "null tree");
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     g.norms_async(g.ws64, 0, nullptr, false, t->stream);
     check(cudaStreamSynchronize(t->stream), "residual norm");
@@ -613,6 +642,7 @@ int afg_adjoint(afg_tree *t, const double *g_leaf, double *lambda_leaf, double *
     const afg_mg_opts o = opts_or_default(opts);
     if (int rc = validate(o)) return rc;
     AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     const auto t0 = clk::now();
     double rel = 0.0;
@@ -640,8 +670,12 @@ int afg_forest_create(int n, afg_tree *const *trees, afg_forest **out) {
     for (int i = 0; i < n; ++i)
         if (!trees[i] || trees[i]->ht.D != trees[0]->ht.D || trees[i]->ht.N != trees[0]->ht.N)
             return fail(AFG_ERR_ARG, "trees must exist and share dim and box_n");
+    for (int i = 0; i < n; ++i)
+        if (trees[i]->ht.nroots() != 1)
+            return fail(AFG_ERR_STATE, "a forest cannot hold trees of several root boxes");
     AFG_API_BEGIN
     std::unique_ptr<afg_forest> f(new afg_forest);
+    f->device = afg::current_device();
     std::vector<const HostTree *> v;
     for (int i = 0; i < n; ++i) {
         f->trees.emplace_back(new HostTree(trees[i]->ht));
@@ -676,6 +710,7 @@ int afg_forest_counts(const afg_forest *f, long long *cells, long long *faces) {
 int afg_forest_set_rhs(afg_forest *f, const double *rho) {
     if (!f || !rho) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_FOREST_DEVICE(f);
     Grid &g = *f->grid;
     afg::launch_leaf_set(g.leaf_cfg(true, f->stream), g.meta, g.d_leaves, g.n_leaf_boxes, rho, g.ws64.rho->p);
     g.leaf_rho_hat(g.ws64, f->stream);
@@ -688,6 +723,7 @@ int afg_forest_set_rhs(afg_forest *f, const double *rho) {
 int afg_forest_set_dirichlet(afg_forest *f, const double *b) {
     if (!f || !b) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_FOREST_DEVICE(f);
     set_dirichlet_dev(*f->grid, b, f->stream);
     check(cudaGetLastError(), "afg_forest_set_dirichlet");
     return AFG_OK;
@@ -697,6 +733,7 @@ int afg_forest_set_dirichlet(afg_forest *f, const double *b) {
 int afg_forest_get_solution(const afg_forest *f, double *u) {
     if (!f || !u) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
+    AFG_ON_FOREST_DEVICE(f);
     Grid &g = *f->grid;
     afg::launch_leaf_get(g.leaf_cfg(true, f->stream), g.meta, g.d_leaves, g.n_leaf_boxes, g.ws64.u->p, u);
     check(cudaGetLastError(), "afg_forest_get_solution");
@@ -709,6 +746,7 @@ int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree
     const afg_mg_opts o = opts_or_default(opts);
     if (int rc = validate(o)) return rc;
     AFG_API_BEGIN
+    AFG_ON_FOREST_DEVICE(f);
     Grid &g = *f->grid;
     if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
     const auto t0 = clk::now();
@@ -738,21 +776,21 @@ int afg_kernel_launches(unsigned long long *count) {
     return AFG_OK;
 }
 
-int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
-                    double *flops, long long *cells) {
-    if (!t || reps < 1 || kernel < 0 || kernel > 4) return fail(AFG_ERR_ARG, "bad arguments");
-    AFG_API_BEGIN
-    Grid &g = grid_of(t);
+}  // extern "C"
+
+namespace {
+// times `reps` launches of one kernel of the solve on grid g (afg_time_kernel)
+int time_kernel_on(Grid &g, cudaStream_t s, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
+                   double *flops, long long *cells) {
     if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
     if (kernel < 3 && (level < g.lmin || level > g.lmax)) return fail(AFG_ERR_ARG, "level out of range");
     if ((kernel == 1 || kernel == 2) && level < 2) return fail(AFG_ERR_ARG, "level must be >= 2");
     if (!fp64 || kernel == 3) g.ensure_mixed();
     afg::Workspace &w = fp64 ? g.ws64 : g.ws32;
     if (!fp64) {  // FP32 data from the FP64 source (values are irrelevant to timing)
-        afg::launch_leaf_residual(g.leaf_cfg(true, t->stream), g.meta, g.d_leaves, g.n_leaf_boxes, g.ws64.u->p,
+        afg::launch_leaf_residual(g.leaf_cfg(true, s), g.meta, g.d_leaves, g.n_leaf_boxes, g.ws64.u->p,
                                   g.ws64.rho->p, 0, g.d_norms, g.d_norms + g.T, g.ws32.rho->p, true);
     }
-    cudaStream_t s = t->stream;
     const double sz = fp64 ? 8.0 : 4.0;
     const int D = g.D;
     long long nc = 0;
@@ -810,7 +848,29 @@ int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, doub
     if (flops) *flops = fl;
     if (cells) *cells = nc;
     return AFG_OK;
+}
+}  // namespace
+
+
+extern "C" {
+
+int afg_time_kernel(afg_tree *t, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
+                    double *flops, long long *cells) {
+    if (!t || reps < 1 || kernel < 0 || kernel > 4) return fail(AFG_ERR_ARG, "bad arguments");
+    AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
+    return time_kernel_on(grid_of(t), t->stream, kernel, level, fp64, reps, avg_ms, bytes, flops, cells);
+    AFG_API_END
+}
+
+int afg_forest_time_kernel(afg_forest *f, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
+                           double *flops, long long *cells) {
+    if (!f || reps < 1 || kernel < 0 || kernel > 4) return fail(AFG_ERR_ARG, "bad arguments");
+    AFG_API_BEGIN
+    AFG_ON_FOREST_DEVICE(f);
+    return time_kernel_on(*f->grid, f->stream, kernel, level, fp64, reps, avg_ms, bytes, flops, cells);
     AFG_API_END
 }
 
 }  // extern "C"
+

@@ -2,6 +2,7 @@
 // multigrid drivers of arXiv:1701.04329 Sec. 3.2 on top of the kernels.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <stdexcept>
 
@@ -18,13 +19,56 @@ void check(cudaError_t e, const char *what) {
     throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-DevBuf::DevBuf(size_t n) : bytes(n) {
+Allocator &allocator() {
+    static Allocator a;
+    return a;
+}
+int g_user_buffers = 0;
+
+DeviceGuard::DeviceGuard(int dev) {
+    int cur = 0;
+    check(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != dev) {
+        check(cudaSetDevice(dev), "cudaSetDevice");
+        prev = cur;
+    }
+}
+
+DeviceGuard::~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+int current_device() {
+    int d = 0;
+    check(cudaGetDevice(&d), "cudaGetDevice");
+    return d;
+}
+
+DevBuf::DevBuf(size_t n) : bytes(n), from(allocator()) {
     if (n == 0) return;
-    check(cudaMalloc(&p, n), "cudaMalloc");
+    if (!from.alloc) {
+        check(cudaMalloc(&p, n), "cudaMalloc");
+        return;
+    }
+    p = from.alloc(n, from.ctx);
+    if (!p) throw NoMem("the allocator callback returned NULL for " + std::to_string(n) + " bytes");
+    ++g_user_buffers;
+    if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+        from.dealloc(p, from.ctx);
+        --g_user_buffers;
+        p = nullptr;
+        throw std::runtime_error("the allocator callback returned memory that is not 256-byte aligned");
+    }
 }
 
 DevBuf::~DevBuf() {
-    if (p) cudaFree(p);
+    if (!p) return;
+    if (from.alloc) {
+        from.dealloc(p, from.ctx);
+        --g_user_buffers;
+    } else {
+        cudaFree(p);
+    }
 }
 
 namespace {
@@ -37,18 +81,25 @@ T *upload(const std::vector<T> &v, std::vector<std::unique_ptr<DevBuf>> &owned) 
 }  // namespace
 
 Grid::Grid(const std::vector<const HostTree *> &trees) {
+    device = current_device();
     // the device hierarchy below level 1 holds one box per tree (the root's
     // coarse grids, solved in one block); a block of several root boxes needs
     // coarse levels of several connected boxes, which the device path lacks
     for (const HostTree *h : trees)
         if (h->nroots() != 1 && trees.size() > 1)
             throw std::runtime_error("a forest cannot hold trees of several root boxes");
+    // (afg_forest_create refuses such trees in a forest of any size)
     D = trees[0]->D;
     N = trees[0]->N;
     T = (int)trees.size();
     block = trees[0]->nroots() != 1;
-    if (block && bottom_block_smem(trees[0]->D, true, trees[0]->N, trees[0]->nr, trees[0]->bct) > 227 * 1024)
-        throw std::runtime_error("the block of root boxes is too large for the one-CTA bottom solve");
+    if (block) {
+        const size_t need = bottom_block_smem(trees[0]->D, true, trees[0]->N, trees[0]->nr, trees[0]->bct);
+        if (need > max_smem_optin())
+            throw std::runtime_error("the block of root boxes is too large for the one-CTA bottom solve (" +
+                                     std::to_string(need) + " bytes of shared memory, " +
+                                     std::to_string(max_smem_optin()) + " available)");
+    }
     int nsub = 0;
     if (!block)
         for (int m = N / 2; m >= 2; m /= 2) ++nsub;
@@ -144,8 +195,15 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     // that user face arrays map onto it directly; then the coarse boxes' faces.
     std::vector<int> bcoff(nbox * S, -1), leaves;
     long long off = 0;
+    std::vector<double> leaf_geo;
     for (int t = 0; t < T; ++t)
-        for (int b : trees[t]->leaves) leaves.push_back(gid[t][b]);
+        for (int b : trees[t]->leaves) {
+            leaves.push_back(gid[t][b]);
+            const HBox &hx = trees[t]->boxes[b];
+            const double hh = 1.0 / std::ldexp((double)N, hx.level - 1);
+            for (int a = 0; a < 3; ++a) leaf_geo.push_back(a < D ? (hx.idx[a] - 1) * N * hh : 0.0);
+            leaf_geo.push_back(hh);
+        }
     n_leaf_boxes = (int)leaves.size();
     const int F = D == 2 ? N : N * N;
     for (int g : leaves)
@@ -208,6 +266,7 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     meta.active = nullptr;
     d_child = upload(child, own);
     d_leaves = upload(leaves, own);
+    d_leaf_geo = upload(leaf_geo, own);
     // boxes (level >= 2) whose parent has a same-level leaf across a face
     std::vector<int> cfc;
     for (auto &v : lv) {
@@ -250,6 +309,9 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
 }
 
 Grid::~Grid() {
+    // cudaFree waits for the device; a caller's deallocator may hand the
+    // memory to other work at once, so wait for this grid's kernels first
+    if (allocator().alloc || g_user_buffers > 0) cudaDeviceSynchronize();
     clear_graphs();
     if (h_norms) cudaFreeHost(h_norms);
     if (h_nactive) cudaFreeHost(h_nactive);

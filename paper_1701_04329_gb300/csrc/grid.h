@@ -25,9 +25,34 @@ struct NoMem : std::runtime_error {
 
 void check(cudaError_t e, const char *what);
 
+// Where device buffers come from: cudaMalloc/cudaFree, or the caller's
+// callbacks (afg_set_allocator).  Process-wide; a buffer is returned to the
+// allocator that made it.
+struct Allocator {
+    void *(*alloc)(size_t bytes, void *ctx) = nullptr;
+    void (*dealloc)(void *ptr, void *ctx) = nullptr;
+    void *ctx = nullptr;
+};
+Allocator &allocator();
+// buffers made by a caller's allocator that are alive (the library synchronises
+// the device before it hands one back)
+extern int g_user_buffers;
+
+// Makes `dev` the current device for the lifetime of the guard (the device a
+// handle's data lives on) and restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+int current_device();
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    Allocator from;
     DevBuf() = default;
     explicit DevBuf(size_t n);
     DevBuf(const DevBuf &) = delete;
@@ -51,6 +76,7 @@ class Grid {
   public:
     explicit Grid(const std::vector<const HostTree *> &trees);
     ~Grid();
+    int device = 0;  // the CUDA device holding this grid's data
 
     struct Level {
         int l, M, MP, b0, nb;  // MP = parent box size (0 at the bottom)
@@ -75,6 +101,7 @@ class Grid {
 
     BoxMeta meta{};  // active = nullptr
     int *d_leaves = nullptr;  // all leaf boxes, canonical (tree-major) order
+    double *d_leaf_geo = nullptr;  // per leaf box (canonical order): lower corner x, y, z and cell size
     int *d_cf_children = nullptr;  // children of parents that face a same-level leaf
     int n_cf_children = 0;
     int *d_child = nullptr;
@@ -126,5 +153,8 @@ class Grid {
     std::map<std::tuple<int, int, int, int, int>, int> graph_kernels;  // kernel nodes per graph
     void clear_graphs();
 };
+
+// leaf cell centres (canonical order, D doubles per cell) into device memory
+void launch_cell_centers(const Grid &g, double *xyz, cudaStream_t s);
 
 }  // namespace afg

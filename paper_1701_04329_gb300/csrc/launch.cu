@@ -1,6 +1,7 @@
 // Dimension dispatch of the launch layer and the occupancy cache.
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "launch_impl.cuh"
@@ -16,21 +17,34 @@ extern template struct PrecOps<3, float>;
 
 unsigned long long g_launches = 0;
 
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
-    }
-    return n;
+namespace {
+int device_attr(cudaDeviceAttr a, int fallback) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;  // (device, attribute) -> value
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(dev, (int)a);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, a, dev) != cudaSuccess || v < 1) v = fallback;
+    cache[key] = v;
+    return v;
 }
+}  // namespace
+
+int sm_count() { return device_attr(cudaDevAttrMultiProcessorCount, 1); }
+
+size_t max_smem_optin() { return (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 48 * 1024); }
 
 int occupancy(const void *kernel, size_t smem) {
     static std::mutex mu;
-    static std::map<std::pair<const void *, size_t>, int> cache;
+    static std::map<std::tuple<int, const void *, size_t>, int> cache;  // per device: the attribute is too
+    int dev = 0;
+    cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
-    auto key = std::make_pair(kernel, smem);
+    auto key = std::make_tuple(dev, kernel, smem);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -33,6 +33,8 @@ void launch_bottom_block(const LaunchCfg &, const BoxMeta &, const int *nroot, c
                          int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom);
 // shared memory that launch needs (bytes)
 size_t bottom_block_smem(int D, bool fp64, int N, const int *nroot, const int *bct);
+// opt-in shared memory per block of the current device (bytes)
+size_t max_smem_optin();
 // rhoh (may be null): use the pre-scaled source -h^2 rho/(2D) instead of rho
 void launch_smooth(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *u, const void *rho,
                    const void *rhoh, double h2, int colour, int hom);

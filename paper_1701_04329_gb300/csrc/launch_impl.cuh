@@ -274,7 +274,7 @@ void do_bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, con
     for (int s = 0; s < 6; ++s) B.bct[s] = s < 2 * D ? bct[s] : 0;
     B.root_box = root_box;
     const size_t smem = block_bottom_smem<D, T>(N, B);
-    if (smem > 227 * 1024)
+    if (smem > max_smem_optin())
         throw std::runtime_error("the block of root boxes is too large for one CTA's shared memory (" +
                                  std::to_string(smem) + " bytes)");
     auto k = k_bottom_block<D, T>;

@@ -34,8 +34,18 @@ extern "C" int afg_forest_residual_norms_noalloc(afg_forest *f, double *max_abs_
     afg::Grid &g = *f->grid;
     if (g.T > kNoAllocMaxTrees)
         return noalloc_fail(AFG_ERR_ARG, "forest has more trees than the 1024 the allocation-free norm supports");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(AFG_ERR_CUDA, "cudaGetDevice failed");
+    if (!g.rhs_set) return noalloc_fail(AFG_ERR_STATE, "no right-hand side set");
+    // the forest's device (where its data and this call's kernels live)
+    const int dev = f->device;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return noalloc_fail(AFG_ERR_CUDA, "cudaGetDevice failed");
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return noalloc_fail(AFG_ERR_CUDA, "cudaSetDevice failed");
+    struct Restore {
+        int prev, dev;
+        ~Restore() {
+            if (prev != dev) cudaSetDevice(prev);
+        }
+    } restore{prev, dev};
     unsigned long long *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -52,7 +62,7 @@ extern "C" int afg_forest_residual_norms_noalloc(afg_forest *f, double *max_abs_
     }
     try {
         cudaStream_t s = f->stream;
-        g.restrict_all(g.ws64, s);
+        g.restrict_cf(g.ws64, s);  // what the composite residual reads, as afg_forest_solve's norms
         // the scratch keeps the previous call's maxima: clear the slots used
         afg::check(cudaMemsetAsync(scratch, 0, 2 * (size_t)g.T * sizeof(unsigned long long), s), "memset");
         afg::launch_leaf_residual(g.leaf_cfg(true, s), g.meta, g.d_leaves, g.n_leaf_boxes, g.ws64.u->p,

@@ -99,3 +99,26 @@ def test_periodic_types_validated_on_the_host():
         assert e.code == afgpu.AFG_ERR_ARG
     t.set_boundary_types([2, 2, 1, 0, 0, 0])  # Neumann/Dirichlet changes stay allowed
     assert t.n_bfaces == 4 * 4 * 64  # no boundary faces on the periodic x sides
+
+
+def test_allocator_needs_both_callbacks():
+    """afg_set_allocator: both callbacks or neither (no GPU involved)."""
+    L = afgpu.lib()
+    f = afgpu.ALLOC_FN(lambda n, c: None)
+    assert L.afg_set_allocator(ctypes.cast(f, ctypes.c_void_p), None, None) == afgpu.AFG_ERR_ARG
+    assert b"both" in L.afg_last_error()
+    assert L.afg_set_allocator(None, None, None) == afgpu.AFG_OK
+
+
+def test_forest_of_a_block_tree_is_refused():
+    """A forest never holds a tree whose level 1 is a block of root boxes,
+    whatever its size; the refusal comes before any device work."""
+    m = afgpu.Tree(2, 8, 3, roots=(2, 1))
+    m.refine_uniform(2)
+    for trees in ([m], [m, afgpu.Tree(2, 8, 3)]):
+        try:
+            afgpu.Forest(trees)
+            assert False, "expected a refusal"
+        except afgpu.AfgError as e:
+            assert e.code == afgpu.AFG_ERR_STATE
+            assert "several root boxes" in str(e)

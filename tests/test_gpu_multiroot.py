@@ -78,3 +78,21 @@ def test_forest_of_root_blocks_is_refused():
         t.refine_uniform(2)
     with pytest.raises(afgpu.AfgError):
         afgpu.Forest([t1, t2])
+
+
+@pytest.mark.parametrize("roots,fits", [((6, 1, 1), True), ((3, 2, 1), True), ((2, 2, 2), False), ((7, 1, 1), False)])
+def test_block_size_limit_of_the_one_cta_bottom(roots, fits):
+    """The documented limit for blocks of 8^3 root boxes (FP64, one CTA's
+    shared memory): 6 x 1 x 1 and 3 x 2 x 1 fit, 2 x 2 x 2 and 7 x 1 x 1 are
+    refused when the device grid is built (the first field call), before
+    any kernel or graph."""
+    t = afgpu.Tree(3, 8, 1, roots=roots)
+    rho = torch.ones(t.n_leaf_cells, dtype=torch.float64, device="cuda")
+    if fits:
+        t.set_rhs(rho)
+        st = t.solve(afgpu.default_opts(rel_tol=1e-8, max_cycles=40))
+        assert st["rel_residual"] <= 1e-8
+    else:
+        with pytest.raises(afgpu.AfgError) as e:
+            t.set_rhs(rho)
+        assert e.value.code == afgpu.AFG_ERR_STATE and "too large" in str(e.value)
