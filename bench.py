@@ -422,38 +422,57 @@ def bench_paper_cmp(K, W_, dev):
     return out
 
 
-def bench_forest(K, W_, dev, hbm):
+def bench_forest(K, W_, dev, hbm, dist=None, rank=0, world=1):
     """configs[3]-style batched workload at the tuner's recorded choice: 512
     quadtrees (seeds 1000+t), mixed precision to 1e-8 per tree, CUDA-graph
-    replay; unknowns/s and the roofline of its FP32 half-sweep."""
+    replay; unknowns/s and the roofline of its FP32 half-sweep.  With N
+    ranks the trees are split by LPT on box count (paper_1701_04329_gb300/
+    shard.py): every rank solves its own forest, nothing is exchanged on the
+    solve path, the time is the slowest rank's (barrier + max over ranks)."""
     import torch
-    from paper_1701_04329_gb300 import afgpu, autotune
+    from paper_1701_04329_gb300 import afgpu, autotune, shard
     choice = autotune.tuned_choice()
     box_n, nd, nu = choice or (16, 2, 2)
-    trees, rho_h, b_h = autotune.build_forest(512, box_n)
-    f = afgpu.Forest(trees)
-    f.set_rhs(torch.tensor(rho_h, device=dev))
-    f.set_dirichlet(torch.tensor(b_h, device=dev))
-    n = int(f.cells.sum())
+    trees, rhos, bs = shard.build_batch(512, box_n)
+    boxes = [t.info().n_boxes for t in trees]
+    bins = shard.lpt_partition(boxes, world)
+    mine = bins[rank]
     opts = afgpu.default_opts(rel_tol=1e-8, precision=afgpu.AFG_MIXED, n_down=nd, n_up=nu, max_cycles=60)
+    res, f = shard.solve_shard(trees, rhos, bs, mine, opts, dev)
+    n_all = int(sum(len(r) for r in rhos))
+    for _ in range(W_):
+        f.solve(opts)
+    torch.cuda.synchronize()
+    barrier(dist)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = afgpu.kernel_launches()
-    ms, st = event_time(lambda: f.solve(opts), K, W_)
-    launches = (afgpu.kernel_launches() - l0) // (K + W_)
-    lv = [tr.info() for tr in trees]
+    e0.record()
+    for _ in range(K):
+        st = f.solve(opts)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = (afgpu.kernel_launches() - l0) // K
+    ms = max_over_ranks(dist, e0.elapsed_time(e1) / K)
+    stats = shard.gather_stats(dist, rank, world, list(zip(mine, st)), len(trees))
+    lv = [trees[i].info() for i in mine]
     top = max(i.highest_level for i in lv)
-    boxes = [sum(i.boxes_per_level[l] for i in lv) for l in range(top + 1)]
-    lvl = max(range(1, top + 1), key=lambda l: boxes[l])
+    per_level = [sum(i.boxes_per_level[l] for i in lv) for l in range(top + 1)]
+    lvl = max(range(1, top + 1), key=lambda l: per_level[l])
     k32 = f.time_kernel(0, lvl, False, 20)
     gbs = k32["bytes"] / (k32["ms"] * 1e-3) / 1e9
     out = {"workload": "512 2D quadtrees (seeds 1000+t), 1-4 Gaussian sources, max level 4..9 (8^2 boxes; one "
                        "fewer with 16^2), mixed precision to 1e-8 per tree, CUDA graph",
-           "config": {"box_n": box_n, "n_down": nd, "n_up": nu, "source": "tuned_forest.json" if choice else "default"},
-           "value": n / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "unknowns": n,
-           "max_cycles": max(s["cycles"] for s in st), "worst_rel_residual": max(s["rel_residual"] for s in st),
+           "config": {"box_n": box_n, "n_down": nd, "n_up": nu, "source": "tuned_forest.json" if choice else "default",
+                      "ranks": world, "split": "whole trees by LPT on box count" if world > 1 else "one forest"},
+           "value": n_all / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "unknowns": n_all,
            "gpu_launches_per_step": launches,
            "roofline": {"bound": "hbm", "kernel": "k_smooth_p<2,%d,float> (half-sweep, level %d, all trees)" % (box_n, lvl),
                         "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "ms": k32["ms"],
                         "algorithmic_bytes": k32["bytes"], "traffic": None}}
+    if stats is not None:
+        out["max_cycles"] = max(s["cycles"] for s in stats)
+        out["worst_rel_residual"] = max(s["rel_residual"] for s in stats)
     f.close()
     for tr in trees:
         tr.close()
@@ -652,13 +671,15 @@ def main():
     # the other workloads, each timed on this GPU (a failure only loses its entry)
     with_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
     K2 = max(1, min(args.steps, 5))
-    extra = (("gauss2d", lambda: bench_gauss2d(K2, args.warmup, dev, with_oracle)),
+    extra = (("forest", lambda: bench_forest(K2, args.warmup, dev, hbm, dist, rank, world)),
+             ("gauss2d", lambda: bench_gauss2d(K2, args.warmup, dev, with_oracle)),
              ("blobs3d_fwd_bwd", lambda: bench_blobs3d(K2, max(1, min(args.warmup, 2)), dev)),
-             ("paper_cmp", lambda: bench_paper_cmp(K2, args.warmup, dev)),
-             ("forest", lambda: bench_forest(K2, args.warmup, dev, hbm)))
+             ("paper_cmp", lambda: bench_paper_cmp(K2, args.warmup, dev)))
     for key, fn in extra:
-        if args.skip_extra or world > 1:  # replicas time the headline workload only
+        if args.skip_extra:
             break
+        if world > 1 and key != "forest":  # the single-tree workloads run as replicas: only the headline
+            continue
         try:
             out[key] = fn()
         except Exception as ex:  # noqa: BLE001 - reported in the JSON line instead

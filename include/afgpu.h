@@ -3,7 +3,8 @@
  * the geometric multigrid method on quadtree/octree AMR grids of
  * Teunissen & Ebert, "Afivo" (arXiv:1701.04329).
  *
- * Problem (Sec. 3, Eq. mg-discr-equation): A_h(u_h) = rho_h on [0,1]^D,
+ * Problem (Sec. 3, Eq. mg-discr-equation): A_h(u_h) = rho_h on [0,1]^D, with
+ * A the Laplacian or div(eps grad u) (Sec. 3.4-3.5, afg_set_operator),
  * D = 2 or 3, with Dirichlet, Neumann or periodic domain sides (at least one
  * Dirichlet side), discretised on a tree of boxes of N^D cells (Sec. 1.3,
  * 2.1).  A tree's level 1 may be a block of root boxes (domain [0,r_x] x
@@ -171,6 +172,30 @@ int afg_leaf_levels(const afg_tree *t, int32_t *levels_host);
  * changes by at most one per call.  0 <= n_buf <= box_n. */
 int afg_adapt(afg_tree *t, const int8_t *flags_host, int n_buf, int *n_added, int *n_removed);
 
+/* Mesh adaptation that carries the solution along (Sec. 2.3: prolongation
+ * and restriction are applied when the mesh changes): the tree is adapted as
+ * by afg_adapt, and the current solution on the device moves to the new
+ * leaves -- a leaf that stays keeps its values, a box whose children are
+ * removed gets their mean (Sec. 2.5), and the children of a refined leaf are
+ * prolonged from it with `scheme` (AFG_PROLONG_*), its ghost values filled
+ * as in the solver (the stored boundary data, the refinement-boundary scheme
+ * of Sec. 3.3, and for the bi/trilinear scheme the edge/corner ghosts of
+ * Sec. 2.4).  The other field data (rho, boundary data, eps) must be set
+ * again.  Needs the tree's field data on the device (AFG_ERR_STATE
+ * otherwise); synchronises the tree's stream. */
+int afg_adapt_transfer(afg_tree *t, const int8_t *flags_host, int n_buf, int scheme, int *n_added, int *n_removed);
+
+/* Refinement flags computed on the device (the criterion of Sec. 4.1 is of
+ * this form: refine where h^2 |rho| exceeds a threshold): for every leaf
+ * cell, with h its cell size, flags = +1 where |f| h^power > tau_refine,
+ * -1 where |f| h^power < tau_coarsen, 0 elsewhere.  f_dev: a leaf field
+ * (n_leaf_cells doubles, canonical order), flags_dev: n_leaf_cells int8,
+ * both device memory, on the tree's stream; copy the flags to the host for
+ * afg_adapt / afg_adapt_transfer.  AFG_ERR_ARG unless 0 <= power <= 8 and
+ * tau_coarsen <= tau_refine. */
+int afg_flag_cells(afg_tree *t, const double *f_dev, int power, double tau_refine, double tau_coarsen,
+                   int8_t *flags_dev);
+
 int afg_info(const afg_tree *t, afg_tree_info *out);
 
 /* Tree arrays in canonical box order (host memory): level[n], spatial index
@@ -209,6 +234,46 @@ int afg_set_rhs(afg_tree *t, const double *rho_leaf_dev);
  * normal derivatives (ghost u + h b).  Coarse boxes use face averages.
  * Without this call the boundary data is zero. */
 int afg_set_dirichlet(afg_tree *t, const double *b_face_dev);
+/* Operator of the tree (Sec. 3.4-3.5).  AFG_OP_LAPLACE (default): the
+ * Laplacian.  AFG_OP_VAR: div(eps grad u) with eps > 0 per leaf cell; the
+ * flux through a face between cells of coefficients e1 and e2 is the
+ * harmonic mean 2 e1 e2 / (e1 + e2) times the difference quotient (Sec. 3.4).
+ * AFG_OP_VAR_RZ (2D only): the same in cylindrical (r,z) coordinates with
+ * r = x, (1/r) d/dr (r eps du/dr) + d/dz (eps du/dz): the r-faces are weighted
+ * by r_face / r_cell, so the -x side (the axis r = 0) carries no flux (Sec.
+ * 3.5).  Coarse cells take the mean of their children's eps; in (r,z) every
+ * restriction (u, residual, eps) is the mean weighted by the children's r.
+ * Ghost eps: the same-level neighbour's, the coarse cell's across a
+ * refinement boundary, the cell's own at the domain boundary; Neumann data
+ * stays the normal derivative of u (flux eps b).  The coarse-grid correction
+ * keeps the linear prolongation.  Host call; changing it keeps the field data
+ * but requires afg_set_eps again.  AFG_ERR_ARG for an unknown op, (r,z) on a
+ * 3D tree or with a periodic -x side, and for trees of several root boxes.
+ * Not covered with these operators: afg_adjoint and
+ * afg_forest_residual_norms_noalloc (AFG_ERR_STATE), afg_time_kernel. */
+#define AFG_OP_LAPLACE 0
+#define AFG_OP_VAR 1
+#define AFG_OP_VAR_RZ 2
+int afg_set_operator(afg_tree *t, int op);
+/* Prolongation of the coarse-grid correction (Sec. 2.5): AFG_PROLONG_LINEAR
+ * (default; the 2-1-1 / 1-1-1-1 scheme, exact for linear fields, the one
+ * Sec. 4.1 calls first order), AFG_PROLONG_MULTILINEAR (bilinear / trilinear:
+ * per axis weight 3/4 for the nearer coarse cell, 1/4 for the farther one;
+ * it reads the coarse difference's edge and corner ghosts, Sec. 2.4: copied
+ * from the diagonal same-level neighbour, else extrapolated linearly) or
+ * AFG_PROLONG_ZEROTH (the coarse cell's value).  With a non-default scheme
+ * every level, the coarse grids below the root included, runs on the
+ * per-level kernels.  Host call; AFG_ERR_ARG for an unknown scheme or a tree
+ * of several root boxes. */
+#define AFG_PROLONG_LINEAR 0
+#define AFG_PROLONG_MULTILINEAR 1
+#define AFG_PROLONG_ZEROTH 2
+int afg_set_prolongation(afg_tree *t, int scheme);
+
+/* eps > 0 on leaf cells (n_leaf_cells doubles, canonical order, device
+ * memory): stored on the leaves and restricted to every coarser level. */
+int afg_set_eps(afg_tree *t, const double *eps_leaf_dev);
+
 /* Initial guess / warm start on leaf cells; without it the guess is zero. */
 int afg_set_solution(afg_tree *t, const double *u_leaf_dev);
 int afg_get_solution(const afg_tree *t, double *u_leaf_dev);
@@ -247,6 +312,9 @@ int afg_forest_set_stream(afg_forest *f, void *cuda_stream);
 int afg_forest_counts(const afg_forest *f, long long *leaf_cells_per_tree, long long *bfaces_per_tree);
 int afg_forest_set_rhs(afg_forest *f, const double *rho_dev);
 int afg_forest_set_dirichlet(afg_forest *f, const double *b_dev);
+/* eps of every tree (the trees' shared operator, afg_set_operator before
+ * afg_forest_create), forest canonical order. */
+int afg_forest_set_eps(afg_forest *f, const double *eps_dev);
 int afg_forest_get_solution(const afg_forest *f, double *u_dev);
 /* Solve every tree to opts->rel_tol; a converged tree is masked out of
  * later cycles.  per_tree (may be NULL) receives n stats records. */

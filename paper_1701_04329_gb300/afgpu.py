@@ -18,6 +18,8 @@ AFG_OK, AFG_ERR_ARG, AFG_ERR_CUDA, AFG_ERR_NOMEM, AFG_ERR_STATE, AFG_ERR_NOT_CON
     0, -1, -2, -3, -4, -5, -6)
 AFG_BC_DIRICHLET, AFG_BC_NEUMANN, AFG_BC_PERIODIC = 0, 1, 2
 AFG_FP64, AFG_MIXED = 0, 1
+AFG_OP_LAPLACE, AFG_OP_VAR, AFG_OP_VAR_RZ = 0, 1, 2
+AFG_PROLONG_LINEAR, AFG_PROLONG_MULTILINEAR, AFG_PROLONG_ZEROTH = 0, 1, 2
 
 
 class AfgError(RuntimeError):
@@ -70,6 +72,9 @@ _SIGS = {
     "afg_set_allocator": (I, [P, P, P]), "afg_cell_centers_device": (I, [P, P]),
     "afg_forest_time_kernel": (I, [P, I, I, I, I, P, P, P, P]),
     "afg_autotune": (I, [P, I, P, ctypes.c_char_p, P, ctypes.c_size_t]),
+    "afg_set_operator": (I, [P, I]), "afg_set_eps": (I, [P, P]), "afg_forest_set_eps": (I, [P, P]),
+    "afg_set_prolongation": (I, [P, I]), "afg_adapt_transfer": (I, [P, P, I, I, P, P]),
+    "afg_flag_cells": (I, [P, P, I, DBL, DBL, P]),
 }
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -254,6 +259,26 @@ class Tree:
         _check(lib().afg_adapt(self._h, fp, n_buf, ctypes.byref(a), ctypes.byref(r)))
         return a.value, r.value
 
+    def flag_cells(self, f, power=2, tau_refine=1e-3, tau_coarsen=-1.0):
+        """afg_flag_cells: int8 CUDA tensor of refinement flags from the leaf
+        field f (+1 where |f| h^power > tau_refine, -1 below tau_coarsen)."""
+        import torch
+        self._sync_stream()
+        out = torch.empty(self.n_leaf_cells, dtype=torch.int8, device="cuda")
+        _check(lib().afg_flag_cells(self._h, _dev(f, self.n_leaf_cells), int(power), float(tau_refine),
+                                    float(tau_coarsen), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def adapt_transfer(self, flags, n_buf=2, scheme=AFG_PROLONG_LINEAR):
+        """afg_adapt_transfer: adapt and carry the device solution along."""
+        f, fp = _np(flags, np.int8)
+        if f.size != self.n_leaf_cells:
+            raise ValueError("need one flag per leaf cell")
+        self._sync_stream()
+        a, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().afg_adapt_transfer(self._h, fp, n_buf, int(scheme), ctypes.byref(a), ctypes.byref(r)))
+        return a.value, r.value
+
     def export(self):
         info = self.info()
         n, D = info.n_boxes, self.D
@@ -285,6 +310,20 @@ class Tree:
         if t.size != 2 * self.D:
             raise ValueError("need %d boundary types" % (2 * self.D))
         _check(lib().afg_set_boundary_types(self._h, t.ctypes.data_as(P)))
+
+    def set_operator(self, op):
+        """AFG_OP_LAPLACE, AFG_OP_VAR (div(eps grad u), Sec. 3.4) or
+        AFG_OP_VAR_RZ ((r,z) coordinates, Sec. 3.5); then set eps."""
+        _check(lib().afg_set_operator(self._h, int(op)))
+
+    def set_eps(self, eps):
+        self._sync_stream()
+        _check(lib().afg_set_eps(self._h, _dev(eps, self.n_leaf_cells)))
+
+    def set_prolongation(self, scheme):
+        """AFG_PROLONG_LINEAR (default), AFG_PROLONG_MULTILINEAR or
+        AFG_PROLONG_ZEROTH for the coarse-grid correction (Sec. 2.5)."""
+        _check(lib().afg_set_prolongation(self._h, int(scheme)))
 
     def set_solution(self, u):
         self._sync_stream()
@@ -375,6 +414,10 @@ class Forest:
     def set_dirichlet(self, b):
         self._sync_stream()
         _check(lib().afg_forest_set_dirichlet(self._h, _dev(b, int(self.faces.sum()))))
+
+    def set_eps(self, eps):
+        self._sync_stream()
+        _check(lib().afg_forest_set_eps(self._h, _dev(eps, int(self.cells.sum()))))
 
     def get_solution(self, out=None):
         import torch

@@ -110,8 +110,17 @@ Grid &grid_of(afg_tree *t) {
         std::vector<const HostTree *> v{&t->ht};
         t->grid.reset(new Grid(v));
         t->grid_version = t->ht.version;
+        t->grid->op = t->op;
+        t->grid->prolong = t->prolong;
     }
     return *t->grid;
+}
+
+// the multigrid calls need rho, and eps for the variable-coefficient operators
+int ready(const Grid &g) {
+    if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
+    if (g.op && !g.eps_set) return fail(AFG_ERR_STATE, "the variable-coefficient operator needs eps (afg_set_eps)");
+    return AFG_OK;
 }
 
 double as_double(unsigned long long bits) {
@@ -477,6 +486,79 @@ int afg_adapt(afg_tree *t, const int8_t *flags, int n_buf, int *n_added, int *n_
     AFG_API_END
 }
 
+int afg_adapt_transfer(afg_tree *t, const int8_t *flags, int n_buf, int scheme, int *n_added, int *n_removed) {
+    if (!t || !flags) return fail(AFG_ERR_ARG, "null argument");
+    if (scheme < 0 || scheme > 2) return fail(AFG_ERR_ARG, "scheme must be AFG_PROLONG_LINEAR, _MULTILINEAR or _ZEROTH");
+    if (!t->grid || t->grid_version != t->ht.version)
+        return fail(AFG_ERR_STATE, "no solution on the device to carry over (set or solve one first)");
+    AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
+    Grid &old = *t->grid;
+    cudaStream_t s = t->stream;
+    old.restrict_all(old.ws64, s);  // a parent whose children go away becomes a leaf holding their mean
+    const HostTree before(t->ht);
+    std::string err;
+    int added = 0, removed = 0;
+    const int rc = t->ht.adapt(flags, n_buf, &added, &removed, err);
+    if (rc == -1) return fail(AFG_ERR_ARG, err);
+    if (rc) return fail(AFG_ERR_STATE, err);
+    if (n_added) *n_added = added;
+    if (n_removed) *n_removed = removed;
+    std::unique_ptr<Grid> fresh;
+    {
+        std::vector<const HostTree *> v{&t->ht};
+        fresh.reset(new Grid(v));
+        fresh->op = t->op;
+        fresh->prolong = t->prolong;
+    }
+    // per new leaf: the old box that holds its values, or the old leaf it is prolonged from
+    const HostTree &now = t->ht;
+    const int N = now.N, D = now.D, old_b1 = old.L(1).b0;
+    std::vector<int> src(now.leaves.size()), poff(now.leaves.size());
+    for (size_t li = 0; li < now.leaves.size(); ++li) {
+        const HBox &nb = now.boxes[now.leaves[li]];
+        const int same = before.find(nb.level, nb.idx);
+        if (same >= 0) {
+            src[li] = old_b1 + same;
+            poff[li] = -1;
+            continue;
+        }
+        int pidx[3] = {1, 1, 1}, po = 0;
+        for (int a = 0; a < D; ++a) {
+            pidx[a] = (nb.idx[a] + 1) / 2;
+            po |= (((nb.idx[a] - 1) & 1) * (N / 2)) << (8 * a);
+        }
+        const int par = before.find(nb.level - 1, pidx);
+        if (par < 0 || !before.boxes[par].leaf()) throw std::runtime_error("adapted leaf without a source box");
+        src[li] = old_b1 + par;
+        poff[li] = po;
+    }
+    afg::DevBuf d_src(src.size() * sizeof(int)), d_poff(poff.size() * sizeof(int));
+    check(cudaMemcpyAsync(d_src.p, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, s), "plan");
+    check(cudaMemcpyAsync(d_poff.p, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice, s), "plan");
+    afg::launch_transfer(D, s, N, old.meta, old.ws64.u->as<double>(), old.d_nball, fresh->meta,
+                         fresh->ws64.u->as<double>(), fresh->d_leaves, d_src.as<int>(), d_poff.as<int>(),
+                         (int)src.size(), scheme);
+    check(cudaGetLastError(), "afg_adapt_transfer");
+    check(cudaStreamSynchronize(s), "afg_adapt_transfer");
+    t->grid = std::move(fresh);
+    t->grid_version = t->ht.version;
+    return AFG_OK;
+    AFG_API_END
+}
+
+int afg_flag_cells(afg_tree *t, const double *f_dev, int power, double tau_refine, double tau_coarsen,
+                   int8_t *flags_dev) {
+    if (!t || !f_dev || !flags_dev) return fail(AFG_ERR_ARG, "null argument");
+    if (power < 0 || power > 8 || !(tau_coarsen <= tau_refine)) return fail(AFG_ERR_ARG, "bad power or thresholds");
+    AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
+    Grid &g = grid_of(t);
+    afg::launch_flag(g, f_dev, power, tau_refine, tau_coarsen, reinterpret_cast<signed char *>(flags_dev), t->stream);
+    return AFG_OK;
+    AFG_API_END
+}
+
 int afg_set_boundary_types(afg_tree *t, const int *types) {
     if (!t || !types) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
@@ -538,6 +620,62 @@ int afg_set_rhs(afg_tree *t, const double *rho) {
     AFG_API_END
 }
 
+int afg_set_operator(afg_tree *t, int op) {
+    if (!t) return fail(AFG_ERR_ARG, "null tree");
+    if (op < 0 || op > 2) return fail(AFG_ERR_ARG, "op must be AFG_OP_LAPLACE, AFG_OP_VAR or AFG_OP_VAR_RZ");
+    if (op == 2 && t->ht.D != 2) return fail(AFG_ERR_ARG, "(r,z) coordinates need a 2D tree");
+    if (op && t->ht.nroots() != 1) return fail(AFG_ERR_ARG, "the variable-coefficient operators need a single root box");
+    if (op == 2 && t->ht.bct[0] == 2) return fail(AFG_ERR_ARG, "(r,z): the -x side is the axis and cannot be periodic");
+    AFG_API_BEGIN
+    t->op = op;
+    if (t->grid) {  // the device data stays; the cycles change (graphs are recaptured) and eps is needed again
+        afg::DeviceGuard dg(t->device);
+        t->grid->op = op;
+        t->grid->eps_set = false;
+        t->grid->clear_graphs();
+    }
+    return AFG_OK;
+    AFG_API_END
+}
+
+int afg_set_prolongation(afg_tree *t, int scheme) {
+    if (!t) return fail(AFG_ERR_ARG, "null tree");
+    if (scheme < 0 || scheme > 2) return fail(AFG_ERR_ARG, "scheme must be AFG_PROLONG_LINEAR, _MULTILINEAR or _ZEROTH");
+    if (scheme && t->ht.nroots() != 1) return fail(AFG_ERR_ARG, "other prolongations need a single root box");
+    AFG_API_BEGIN
+    t->prolong = scheme;
+    if (t->grid) {
+        afg::DeviceGuard dg(t->device);
+        t->grid->prolong = scheme;
+        t->grid->clear_graphs();
+    }
+    return AFG_OK;
+    AFG_API_END
+}
+
+int afg_set_eps(afg_tree *t, const double *eps) {
+    if (!t || !eps) return fail(AFG_ERR_ARG, "null argument");
+    if (!t->op) return fail(AFG_ERR_STATE, "eps needs a variable-coefficient operator (afg_set_operator)");
+    AFG_API_BEGIN
+    AFG_ON_DEVICE(t);
+    Grid &g = grid_of(t);
+    g.set_eps(eps, t->stream);
+    check(cudaGetLastError(), "afg_set_eps");
+    return AFG_OK;
+    AFG_API_END
+}
+
+int afg_forest_set_eps(afg_forest *f, const double *eps) {
+    if (!f || !eps) return fail(AFG_ERR_ARG, "null argument");
+    if (!f->grid->op) return fail(AFG_ERR_STATE, "eps needs a variable-coefficient operator (afg_set_operator)");
+    AFG_API_BEGIN
+    AFG_ON_FOREST_DEVICE(f);
+    f->grid->set_eps(eps, f->stream);
+    check(cudaGetLastError(), "afg_forest_set_eps");
+    return AFG_OK;
+    AFG_API_END
+}
+
 int afg_set_dirichlet(afg_tree *t, const double *b) {
     if (!t || !b) return fail(AFG_ERR_ARG, "null argument");
     AFG_API_BEGIN
@@ -579,7 +717,7 @@ static int one_cycle(afg_tree *t, const afg_mg_opts *opts, afg_stats *st, bool f
     AFG_API_BEGIN
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
-    if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
+    if (int rc = ready(g)) return rc;
     const auto t0 = clk::now();
     const afg::MgOpts mo{o.n_down, o.n_up, o.n_base};
     run(g, {fmg ? 30 : 31, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, t->stream, [&](cudaStream_t cs) {
@@ -607,7 +745,7 @@ int afg_solve(afg_tree *t, const afg_mg_opts *opts, afg_stats *st) {
     AFG_API_BEGIN
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
-    if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
+    if (int rc = ready(g)) return rc;
     const auto t0 = clk::now();
     std::vector<std::vector<double>> hist;
     const int cycles = o.precision == AFG_MIXED ? solve_mixed(g, o, t->stream, hist)
@@ -628,6 +766,7 @@ int afg_residual_norm(afg_tree *t, double *max_abs_r, double *max_abs_rho) {
     AFG_API_BEGIN
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
+    if (g.op && !g.eps_set) return fail(AFG_ERR_STATE, "the variable-coefficient operator needs eps (afg_set_eps)");
     g.norms_async(g.ws64, 0, nullptr, false, t->stream);
     check(cudaStreamSynchronize(t->stream), "residual norm");
     if (max_abs_r) *max_abs_r = as_double(g.h_norms[0]);
@@ -644,6 +783,7 @@ int afg_adjoint(afg_tree *t, const double *g_leaf, double *lambda_leaf, double *
     AFG_API_BEGIN
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
+    if (g.op) return fail(AFG_ERR_STATE, "the adjoint is built for the Laplacian only");
     const auto t0 = clk::now();
     double rel = 0.0;
     const int its = adjoint_solve(g, o, t->stream, g_leaf, &rel);
@@ -670,9 +810,12 @@ int afg_forest_create(int n, afg_tree *const *trees, afg_forest **out) {
     for (int i = 0; i < n; ++i)
         if (!trees[i] || trees[i]->ht.D != trees[0]->ht.D || trees[i]->ht.N != trees[0]->ht.N)
             return fail(AFG_ERR_ARG, "trees must exist and share dim and box_n");
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if (trees[i]->ht.nroots() != 1)
             return fail(AFG_ERR_STATE, "a forest cannot hold trees of several root boxes");
+        if (trees[i]->op != trees[0]->op || trees[i]->prolong != trees[0]->prolong)
+            return fail(AFG_ERR_ARG, "the trees of a forest must share the operator and the prolongation");
+    }
     AFG_API_BEGIN
     std::unique_ptr<afg_forest> f(new afg_forest);
     f->device = afg::current_device();
@@ -682,6 +825,8 @@ int afg_forest_create(int n, afg_tree *const *trees, afg_forest **out) {
         v.push_back(f->trees.back().get());
     }
     f->grid.reset(new Grid(v));
+    f->grid->op = trees[0]->op;
+    f->grid->prolong = trees[0]->prolong;
     *out = f.release();
     return AFG_OK;
     AFG_API_END
@@ -748,7 +893,7 @@ int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree
     AFG_API_BEGIN
     AFG_ON_FOREST_DEVICE(f);
     Grid &g = *f->grid;
-    if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
+    if (int rc = ready(g)) return rc;
     const auto t0 = clk::now();
     check(cudaMemsetAsync(g.ws64.u->p, 0, (size_t)g.ncell * 8, f->stream), "zero");
     std::vector<std::vector<double>> hist;
@@ -783,6 +928,7 @@ namespace {
 int time_kernel_on(Grid &g, cudaStream_t s, int kernel, int level, int fp64, int reps, double *avg_ms, double *bytes,
                    double *flops, long long *cells) {
     if (!g.rhs_set) return fail(AFG_ERR_STATE, "no right-hand side set");
+    if (g.op) return fail(AFG_ERR_STATE, "kernel timing covers the Laplacian's kernels");
     if (kernel < 3 && (level < g.lmin || level > g.lmax)) return fail(AFG_ERR_ARG, "level out of range");
     if ((kernel == 1 || kernel == 2) && level < 2) return fail(AFG_ERR_ARG, "level must be >= 2");
     if (!fp64 || kernel == 3) g.ensure_mixed();

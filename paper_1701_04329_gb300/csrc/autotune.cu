@@ -27,6 +27,7 @@ bool json_ints(const char *js, const char *key, std::vector<int> &out, std::stri
     while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') ++p;
     if (*p != ':') { err = std::string("expected ':' after ") + k; return false; }
     ++p;
+    while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') ++p;
     int depth = 0;
     do {
         if (*p == '[') ++depth;

@@ -142,9 +142,11 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     ncell = cells;
     const int S = 2 * D, NC = 1 << D;
     std::vector<int> nb(nbox * S, -1), parent(nbox, -1), poff(nbox, 0), tree(nbox, 0), child(nbox * NC, -1);
+    const int NDIR = D == 2 ? 8 : 26;
+    std::vector<int> nball((size_t)nbox * NDIR, -1);
     std::vector<long long> coff(nbox, 0);
     std::vector<unsigned char> bflag(nbox, 0);
-    std::vector<double> hb(nbox, 0.0);
+    std::vector<double> hb(nbox, 0.0), x0(nbox, 0.0);  // x0: below level 1 the single root's origin, 0
     for (auto &v : lv) {
         const long long cpb = v.ncell / std::max(1, v.nb);
         for (int i = 0; i < v.nb; ++i) {
@@ -162,11 +164,14 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
             child[g * NC] = i + 1 < nsub ? sub[t][i + 1] : gid[t][0];
             for (int s = 0; s < S; ++s)  // one box per level: its own neighbour across a periodic side
                 if (ht.bct[s] == 2) nb[g * S + s] = g;
+            for (int d = 0; d < NDIR; ++d)  // connected like the root: itself across periodic sides
+                if (ht.boxes[ht.lstart[1]].nb[d] >= 0) nball[(size_t)g * NDIR + d] = g;
         }
         for (int b = 0; b < (int)ht.boxes.size(); ++b) {
             const HBox &hx = ht.boxes[b];
             const int g = gid[t][b];
             tree[g] = t;
+            x0[g] = (hx.idx[0] - 1) * N * hb[g];
             if (hx.level == 1) {
                 parent[g] = nsub > 0 ? sub[t][nsub - 1] : -1;
             } else {
@@ -188,6 +193,8 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
                 }
             }
             bflag[g] = (hx.leaf() ? 0 : BF_REFINED) | (special ? BF_SPECIAL : 0);
+            for (int d = 0; d < NDIR; ++d)
+                if (hx.nb[d] >= 0) nball[(size_t)g * NDIR + d] = gid[t][hx.nb[d]];
             for (int c = 0; c < NC; ++c) child[g * NC + c] = hx.child[c] >= 0 ? gid[t][hx.child[c]] : -1;
         }
     }
@@ -260,6 +267,8 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     meta.tree = upload(tree, own);
     meta.hb = d_hb = upload(hb, own);
     meta.nbase = upload(nbase, own);
+    meta.x0 = d_x0 = upload(x0, own);
+    d_nball = upload(nball, own);
     std::vector<double> ih2(nbox);
     for (int b = 0; b < nbox; ++b) ih2[b] = 1.0 / (hb[b] * hb[b]);
     meta.ih2 = upload(ih2, own);
@@ -362,8 +371,10 @@ void Grid::smooth(Workspace &w, int l, int steps, int hom, const int *active, cu
     A.active = active;
     const LaunchCfg c = cfg(l, w.fp64, s);
     for (int it = 0; it < steps; ++it)
-        for (int col = 0; col < 2; ++col)
-            launch_smooth(c, A, v.b0, v.nb, nullptr, w.u->p, w.rho->p, w.rhoh_p(), v.h * v.h, col, hom);
+        for (int col = 0; col < 2; ++col) {
+            if (op) launch_var_smooth(c, A, v.b0, v.nb, w.u->p, w.rho->p, eps_of(w), col, hom, op);
+            else launch_smooth(c, A, v.b0, v.nb, nullptr, w.u->p, w.rho->p, w.rhoh_p(), v.h * v.h, col, hom);
+        }
 }
 
 // Residual on level l restricted to l-1 with v_H <- I v_h, v'_H <- v_H, then
@@ -373,6 +384,11 @@ void Grid::down_step(Workspace &w, int l, int hom, const int *active, cudaStream
     Level &v = L(l), &vc = L(l - 1);
     BoxMeta A = meta;
     A.active = active;
+    if (op) {
+        launch_var_resid_restrict(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.rho->p, w.vold->p, eps_of(w), hom, op);
+        launch_var_fas(cfg(l - 1, w.fp64, s), A, vc.b0, vc.nb, w.u->p, w.rho->p, w.vold->p, eps_of(w), hom, op);
+        return;
+    }
     launch_resid_restrict(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (v.h * v.h), hom);
     launch_fas(cfg(l - 1, w.fp64, s), A, vc.b0, vc.nb, w.u->p, w.rho->p, w.vold->p, 1.0 / (vc.h * vc.h), hom,
                w.rhoh_p());
@@ -395,16 +411,17 @@ void Grid::bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, co
 // FAS V-cycle (Sec. 3.2) from ltop down to the coarsest grid and back.  The
 // levels at and below the root box run in one launch (k_bottom).
 void Grid::vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
+    if (levels_path()) {
+        vcycle_levels(w, ltop, o, hom, active, s);
+        return;
+    }
     for (int l = ltop; l > 1; --l) {
         smooth(w, l, o.n_down, hom, active, s);
         down_step(w, l, hom, active, s);
     }
     bottom(w, ltop < 1 ? ltop : 1, 0, o, hom, active, s);
-    BoxMeta A = meta;
-    A.active = active;
     for (int l = 2; l <= ltop; ++l) {
-        Level &v = L(l);
-        launch_correct(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p);
+        correct(w, l, active, s);
         smooth(w, l, o.n_up, hom, active, s);
     }
 }
@@ -414,24 +431,18 @@ void Grid::vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *a
 // l-1 and run a V-cycle from l.  In a forest a tree leaves the loop after its
 // own finest level (masked).
 void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s) {
-    for (int l = lmax; l > lmin; --l) {
-        Level &v = L(l);
-        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, nullptr, w.u->p);
-    }
+    for (int l = lmax; l > lmin; --l) restrict_u(w, l, L(l).b0, L(l).nb, nullptr, s);
     for (int l = lmax; l > lmin; --l) down_step(w, l, hom, nullptr, s);
     const size_t es = w.fp64 ? 8 : 4;
     // steps l = lmin..1 in one launch (every tree reaches level 1)
-    bottom(w, 1, 1, o, hom, nullptr, s);
+    if (levels_path()) fmg_low_levels(w, o, hom, s);
+    else bottom(w, 1, 1, o, hom, nullptr, s);
     for (int l = 2; l <= lmax; ++l) {
         Level &v = L(l);
         const int *active = masked ? fmg_mask(l) : nullptr;
         check(cudaMemcpyAsync((char *)w.vold->p + v.c0 * es, (char *)w.u->p + v.c0 * es, v.ncell * es,
                               cudaMemcpyDeviceToDevice, s), "copy v'");
-        if (l > lmin) {
-            BoxMeta A = meta;
-            A.active = active;
-            launch_correct(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p);
-        }
+        if (l > lmin) correct(w, l, active, s);
         vcycle(w, l, o, hom, active, s);
     }
 }
@@ -439,24 +450,81 @@ void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t
 // u restricted to every parent (levels lmax..2), so that leaves next to a
 // refined same-level box see the mean of the fine cells.
 void Grid::restrict_all(Workspace &w, cudaStream_t s) {
-    for (int l = lmax; l >= 2; --l) {
-        Level &v = L(l);
-        launch_restrict_u(cfg(l, w.fp64, s), meta, v.b0, v.nb, nullptr, w.u->p);
+    for (int l = lmax; l >= 2; --l) restrict_u(w, l, L(l).b0, L(l).nb, nullptr, s);
+}
+
+// (r,z): every restriction is the mean weighted by the children's r
+void Grid::restrict_u(Workspace &w, int l, int b0, int n, const int *list, cudaStream_t s) {
+    if (op == 2) launch_var_restrict(cfg(l, w.fp64, s), meta, b0, n, list, w.u->p, op);
+    else launch_restrict_u(cfg(l, w.fp64, s), meta, b0, n, list, w.u->p);
+}
+
+// Variable-coefficient operators: the V-cycle on the per-level kernels all
+// the way down (the coarse grids below the root have one box per tree),
+// N_base steps on the 2^D-cell grid.
+void Grid::vcycle_levels(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
+    for (int l = ltop; l > lmin; --l) {
+        smooth(w, l, o.n_down, hom, active, s);
+        down_step(w, l, hom, active, s);
     }
+    smooth(w, lmin, o.n_base, hom, active, s);
+    for (int l = lmin + 1; l <= ltop; ++l) {
+        correct(w, l, active, s);
+        smooth(w, l, o.n_up, hom, active, s);
+    }
+}
+
+// coarse-grid correction of level l from l-1 with the grid's prolongation
+void Grid::correct(Workspace &w, int l, const int *active, cudaStream_t s) {
+    Level &v = L(l);
+    BoxMeta A = meta;
+    A.active = active;
+    if (prolong) launch_correct_x(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p, d_nball, prolong);
+    else launch_correct(cfg(l, w.fp64, s), A, v.b0, v.nb, w.u->p, w.vold->p);
+}
+
+// the FMG steps l = lmin..1 (Sec. 3.2) for the variable-coefficient operators
+void Grid::fmg_low_levels(Workspace &w, const MgOpts &o, int hom, cudaStream_t s) {
+    const size_t es = w.fp64 ? 8 : 4;
+    for (int l = lmin; l <= 1; ++l) {
+        Level &v = L(l);
+        check(cudaMemcpyAsync((char *)w.vold->p + v.c0 * es, (char *)w.u->p + v.c0 * es, v.ncell * es,
+                              cudaMemcpyDeviceToDevice, s), "copy v'");
+        if (l > lmin) correct(w, l, nullptr, s);
+        vcycle_levels(w, l, o, hom, nullptr, s);
+    }
+}
+
+// eps on the leaves, restricted to every parent (level by level, finest
+// first), and its FP32 copy
+void Grid::set_eps(const double *eps_leaf, cudaStream_t s) {
+    if (!eps64) {
+        eps64.reset(new DevBuf((size_t)ncell * 8));
+        check(cudaMemsetAsync(eps64->p, 0, (size_t)ncell * 8, s), "memset eps");
+    }
+    if (!eps32) eps32.reset(new DevBuf((size_t)ncell * 4));
+    launch_leaf_set(leaf_cfg(true, s), meta, d_leaves, n_leaf_boxes, eps_leaf, eps64->p);
+    for (int l = lmax; l > lmin; --l) launch_var_restrict(cfg(l, true, s), meta, L(l).b0, L(l).nb, nullptr, eps64->p, op);
+    launch_to_f32(eps64->as<double>(), eps32->as<float>(), ncell, s);
+    eps_set = true;
 }
 
 // The composite residual reads a parent's values only where the parent
 // faces a same-level leaf; by 2:1 balance the children of such a parent are
 // leaves, so one pass over their list restricts everything it reads.
 void Grid::restrict_cf(Workspace &w, cudaStream_t s) {
-    if (n_cf_children > 0) launch_restrict_u(cfg(2, w.fp64, s), meta, 0, n_cf_children, d_cf_children, w.u->p);
+    if (n_cf_children > 0) restrict_u(w, 2, 0, n_cf_children, d_cf_children, s);
 }
 
 void Grid::norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s) {
     restrict_cf(w, s);
     check(cudaMemsetAsync(d_norms, 0, 2 * T * sizeof(unsigned long long), s), "memset norms");
-    launch_leaf_residual(leaf_cfg(w.fp64, s), meta, d_leaves, n_leaf_boxes, w.u->p, w.rho->p, hom, d_norms,
-                         d_norms + T, rout, rout_f32);
+    if (op)
+        launch_var_leaf_residual(leaf_cfg(w.fp64, s), meta, d_leaves, n_leaf_boxes, w.u->p, w.rho->p, eps_of(w), hom,
+                                 op, d_norms, d_norms + T, rout, rout_f32);
+    else
+        launch_leaf_residual(leaf_cfg(w.fp64, s), meta, d_leaves, n_leaf_boxes, w.u->p, w.rho->p, hom, d_norms,
+                             d_norms + T, rout, rout_f32);
     check(cudaMemcpyAsync(h_norms, d_norms, 2 * T * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
           "norms to host");
 }

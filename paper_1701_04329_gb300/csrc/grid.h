@@ -117,6 +117,20 @@ class Grid {
 
     std::vector<std::unique_ptr<DevBuf>> owned;  // metadata buffers
     Workspace ws64, ws32, wsadj;
+    // operator (Sec. 3.4-3.5): 0 Laplacian, 1 div(eps grad u), 2 the same in (r,z);
+    // eps on every level (leaves: the user's values, parents: restrictions) in both precisions
+    int op = 0;
+    std::unique_ptr<DevBuf> eps64, eps32;
+    bool eps_set = false;
+    double *d_x0 = nullptr;  // lower x coordinate of every box
+    // prolongation of the coarse-grid correction (Sec. 2.5): 0 linear, 1 bi/trilinear, 2 zeroth order
+    int prolong = 0;
+    int *d_nball = nullptr;  // same-level neighbour of every box in all 3^D - 1 directions, -1 none
+    // variable coefficients or another prolongation: every level on the per-level kernels
+    bool levels_path() const { return op != 0 || prolong != 0; }
+    void correct(Workspace &w, int l, const int *active, cudaStream_t s);
+    const void *eps_of(const Workspace &w) const { return w.fp64 ? eps64->p : eps32->p; }
+    void set_eps(const double *eps_leaf, cudaStream_t s);
     std::vector<std::unique_ptr<DevBuf>> bicg;  // adjoint vectors
     bool rhs_set = false;
 
@@ -141,6 +155,11 @@ class Grid {
     void fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t s);
     void restrict_all(Workspace &w, cudaStream_t s);
     void restrict_cf(Workspace &w, cudaStream_t s);  // only what the composite residual reads
+    // restriction of u from the boxes of level l (or a list) into their parents
+    void restrict_u(Workspace &w, int l, int b0, int n, const int *list, cudaStream_t s);
+    // the cycle on the per-level kernels down to the coarsest grid (no k_bottom)
+    void vcycle_levels(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s);
+    void fmg_low_levels(Workspace &w, const MgOpts &o, int hom, cudaStream_t s);
     // composite residual of ws64 (restriction + leaf residual), norms to host buffer (async)
     void norms_async(Workspace &w, int hom, void *rout, bool rout_f32, cudaStream_t s);
     // convergence mask update against the tolerance stored in d_tol
@@ -156,5 +175,10 @@ class Grid {
 
 // leaf cell centres (canonical order, D doubles per cell) into device memory
 void launch_cell_centers(const Grid &g, double *xyz, cudaStream_t s);
+// refinement flags of the leaf cells from a leaf field (canonical order)
+void launch_flag(const Grid &g, const double *f, int power, double tau_ref, double tau_de, signed char *flags,
+                 cudaStream_t s);
+// dst = (float) src, n values
+void launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
 
 }  // namespace afg

@@ -25,6 +25,8 @@ struct afg_tree {
     std::unique_ptr<afg::Grid> grid;
     int grid_version = -1;
     cudaStream_t stream = nullptr;
+    int op = 0;       // operator: 0 Laplacian, 1 div(eps grad u), 2 the same in (r,z)
+    int prolong = 0;  // correction's prolongation: 0 linear, 1 bi/trilinear, 2 zeroth order
     // CUDA device of the tree's field data: the device current at the first
     // field call; every later call runs there whatever device is current
     int device = -1;

@@ -60,6 +60,7 @@ struct BoxMeta {
     const long long *nbase;  // per side: cells of the neighbour / coarse box, or Dirichlet data offset
     const double *ih2;       // 1/h^2 of every box (an FP64 division costs ~11 FP64-pipe instructions)
     const unsigned char *nmask;  // bit s: side s is a Neumann domain boundary (ghost u + h b, not 2 b - u)
+    const double *x0;        // lower x coordinate of every box (the radius in (r,z) coordinates)
 };
 
 // Metadata of one box, prefetched into shared memory one box ahead.

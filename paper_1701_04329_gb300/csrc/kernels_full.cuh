@@ -495,45 +495,87 @@ __device__ __forceinline__ bool cp_slot(int c, int &x, int &y, int &z) {
     return out <= 1;
 }
 
-template <int D, int M, int MP>
-__device__ __forceinline__ int cp_side(const BoxInfo &I, int x, int y, int z, int (&pc)[3]) {
-    pc[0] = unpack_off(I.poff, 0) + x;
-    pc[1] = unpack_off(I.poff, 1) + y;
-    pc[2] = D == 3 ? unpack_off(I.poff, 2) + z : 0;
-    int side = -1;
-    for (int a = 0; a < D; ++a) {
-        if (pc[a] < 0) side = 2 * a;
-        else if (pc[a] >= MP) side = 2 * a + 1;
-    }
-    return side;
-}
-
-template <int D, int M, int MP, typename T>
-__device__ __forceinline__ void cp_issue(const BoxInfo &I, const T *u, const T *vold, T *st, int lt) {
+// Per-thread staging plan of the parent region, the same for every box of a
+// launch.  With MP = M the parent-relative offset poff is 0 or M/2 per axis
+// (even), so a slot (x, y, z) of the region maps to the parent's storage
+// index rbi(poff + (x, y, z)) = rel(x, y, z) + rbi-offset(poff), colour
+// included; rel is per slot, the poff part per box.  A slot outside the
+// region's interior along axis a lies inside the parent unless poff puts it
+// beyond the parent's side; then it is read from the parent's neighbour at
+// the wrapped coordinate (offset rel + nbd, colour unchanged since M is even)
+// or, at the domain boundary, mirrored to the slot one step inward (offset
+// mir, the other colour).
+template <int D, int M, typename T>
+struct CpPlan {
     using S = CpCfg<D, M, T>;
-    T *U = st, *DU = st + S::C, *DV = DU + S::QCP;
-    for (int v = lt; v < S::NV; v += S::G) cp_async<16>(U + v * S::VEC, u + I.coff + (long long)v * S::VEC);
-    for (int c = lt; c < S::QC; c += S::G) {
-        int x, y, z;
-        if (!cp_slot<D, M>(c, x, y, z)) continue;
-        int pc[3];
-        const int side = cp_side<D, M, MP>(I, x, y, z, pc);
-        long long q;
-        if (side < 0) {
-            q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
-        } else {
-            const int a = side >> 1;
-            if (I.code[side] >= 0) {
-                pc[a] = (side & 1) ? 0 : MP - 1;
-                q = I.base[side] + rbi<D, MP>(pc[0], pc[1], pc[2]);
-            } else {  // domain boundary: the mirrored cell (a refined box has no coarser neighbour);
-                      // its difference enters as -d (Dirichlet) or d (Neumann)
-                pc[a] = (side & 1) ? MP - 1 : 0;
-                q = I.pcoff + rbi<D, MP>(pc[0], pc[1], pc[2]);
+    static constexpr int NQ = (S::QC + S::G - 1) / S::G;
+    // meta: bit 0 valid, bits 1-2 axis (3: inside along every axis), bit 3 high side
+    int rel[NQ], nbd[NQ], mir[NQ], meta[NQ];
+    static __device__ __forceinline__ int rel_of(int x, int y, int z) {
+        constexpr int MH = M / 2;
+        return ((x + y + z + D) & 1) * Geo<D, M>::H + (z * M + y) * MH + (x >> 1);
+    }
+    __device__ __forceinline__ void init(int lt) {
+        constexpr int MH = M / 2;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int c = lt + q * S::G;
+            int x = 0, y = 0, z = 0;
+            meta[q] = 0;
+            rel[q] = nbd[q] = mir[q] = 0;
+            if (c >= S::QC || !cp_slot<D, M>(c, x, y, z)) continue;
+            int a = 3, hi = 0;
+            if (x < 0 || x >= MH) { a = 0; hi = x >= MH; }
+            if (y < 0 || y >= MH) { a = 1; hi = y >= MH; }
+            if (D == 3 && (z < 0 || z >= MH)) { a = 2; hi = z >= MH; }
+            meta[q] = 1 | (a << 1) | (hi << 3);
+            rel[q] = rel_of(x, y, z);
+            if (a < 3) {
+                // wrapping pc_a by -+M moves (pc_x >> 1) by -+M/2, or pc_a * stride by -+M * stride
+                const int wrap = a == 0 ? MH : (a == 1 ? M * MH : M * M * MH);
+                nbd[q] = hi ? -wrap : wrap;
+                const int st = hi ? -1 : 1;  // one step inward
+                mir[q] = rel_of(x + (a == 0 ? st : 0), y + (a == 1 ? st : 0), z + (a == 2 ? st : 0));
             }
         }
-        cp_async<(int)sizeof(T)>(DU + c, u + q);
-        cp_async<(int)sizeof(T)>(DV + c, vold + q);
+    }
+};
+
+// Issues the copies of box I into its stage with the plan: the box's own
+// values (vectors) and, per region slot, the parent's u and v' -- swapped
+// across a Dirichlet domain side, so that DU - DV is the difference with the
+// homogeneous ghost rule (-d Dirichlet, d Neumann) in every slot.
+template <int D, int M, int MP, typename T>
+__device__ __forceinline__ void cp_issue(const CpPlan<D, M, T> &pl, const BoxInfo &I, const T *u, const T *vold,
+                                         T *st, int lt) {
+    static_assert(MP == M, "the staged correction serves levels whose parents have the same box size");
+    using S = CpCfg<D, M, T>;
+    constexpr int MH = M / 2;
+    T *U = st, *DU = st + S::C, *DV = DU + S::QCP;
+    for (int v = lt; v < S::NV; v += S::G) cp_async<16>(U + v * S::VEC, u + I.coff + (long long)v * S::VEC);
+    const int px = unpack_off(I.poff, 0), py = unpack_off(I.poff, 1), pz = D == 3 ? unpack_off(I.poff, 2) : 0;
+    const int poffs = (pz * M + py) * MH + (px >> 1);
+#pragma unroll
+    for (int q = 0; q < CpPlan<D, M, T>::NQ; ++q) {
+        const int m = pl.meta[q];
+        if (!(m & 1)) continue;
+        const int c = lt + q * S::G, a = (m >> 1) & 3, hi = (m >> 3) & 1;
+        long long src = I.pcoff + poffs + pl.rel[q];
+        bool swap = false;
+        if (a < 3) {
+            const int pa = a == 0 ? px : (a == 1 ? py : pz);
+            if (pa == (hi ? MH : 0)) {  // beyond the parent's side
+                const int side = 2 * a + hi;
+                if (I.code[side] >= 0) {
+                    src = I.base[side] + poffs + pl.rel[q] + pl.nbd[q];
+                } else {
+                    src = I.pcoff + poffs + pl.mir[q];
+                    swap = !((I.nmask >> side) & 1);
+                }
+            }
+        }
+        cp_async<(int)sizeof(T)>((swap ? DV : DU) + c, u + src);
+        cp_async<(int)sizeof(T)>((swap ? DU : DV) + c, vold + src);
     }
 }
 
@@ -548,6 +590,8 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
     BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * S::BOX * S::BPC * NST);
     const int stride = gridDim.x * S::BPC;
     const int first = blockIdx.x * S::BPC;
+    CpPlan<D, M, T> pl;
+    pl.init(lt);
     pdl_trigger();
     for (int q = 0; q < NST; ++q)  // static metadata: before the wait
         pinfo_load<D>(A, first + q * stride + g, n, b0, info[q * S::BPC + g], lt, S::G, false);
@@ -556,31 +600,27 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
     __syncthreads();
     auto issue = [&](int q) {
         const BoxInfo &In = info[(q % NI) * S::BPC + g];
-        if (In.b >= 0) cp_issue<D, M, MP, T>(In, u, vold, stages + ((q % NST) * S::BPC + g) * S::BOX, lt);
+        if (In.b >= 0) cp_issue<D, M, MP, T>(pl, In, u, vold, stages + ((q % NST) * S::BPC + g) * S::BOX, lt);
         cp_commit();
     };
     for (int q = 0; q < NST - 1; ++q) issue(q);
     int it = 0;
     for (int base = first; base < n; base += stride, ++it) {
         cp_wait<NST - 2>();
-        __syncthreads();  // this box's copies are visible; the previous stage and metadata slot are free
         const BoxInfo &I = info[(it % NI) * S::BPC + g];
         T *st = stages + ((it % NST) * S::BPC + g) * S::BOX;
-        issue(it + NST - 1);
-        pinfo_load<D>(A, base + NST * stride + g, n, b0, info[((it + NST) % NI) * S::BPC + g], lt, S::G, true);
         T *U = st, *DU = st + S::C;
         const T *DV = DU + S::QCP;
-        if (I.b >= 0) {  // d = v_H - v'_H in place, negated across a Dirichlet domain boundary
-            for (int c = lt; c < S::QC; c += S::G) {
-                int x, y, z;
-                if (!cp_slot<D, M>(c, x, y, z)) continue;
-                int pc[3];
-                const int side = cp_side<D, M, MP>(I, x, y, z, pc);
-                const bool flip = side >= 0 && I.code[side] < 0 && !((I.nmask >> side) & 1);
-                DU[c] = flip ? DV[c] - DU[c] : DU[c] - DV[c];
+        if (I.b >= 0) {  // d = v_H - v'_H in the slots this thread staged (its own copies have landed)
+#pragma unroll
+            for (int q = 0; q < CpPlan<D, M, T>::NQ; ++q) {
+                const int c = lt + q * S::G;
+                if (pl.meta[q] & 1) DU[c] -= DV[c];
             }
         }
-        __syncthreads();
+        __syncthreads();  // the differences are visible; the previous stage and metadata slot are free
+        issue(it + NST - 1);
+        pinfo_load<D>(A, base + NST * stride + g, n, b0, info[((it + NST) % NI) * S::BPC + g], lt, S::G, true);
         // 3D: a child (sx,sy,sz) of coarse cell X gets (1/4)((d0 + d_x(sx)) + (d_y(sy) + d_z(sz))):
         // the 2 x-pair and 4 yz-pair sums of a coarse cell are formed once for its 8 children
         T *PS = st + S::C + 2 * S::QCP;
@@ -611,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
                 const int row = w / NVR, h0 = (w % NVR) * VEC;
                 const int j = row % M, k = D == 2 ? 0 : row / M;
                 const int r = (col + j + k + D) & 1;
-                const int ox = r ? 1 : -1, oy = (j & 1) ? Q : -Q, oz = (k & 1) ? Q * Q : -Q * Q;
+                const int ox = r ? 1 : -1, oy = (j & 1) ? Q : -Q;
                 const int b = D == 2 ? ((j >> 1) + 1) * Q + (h0 + 1) : (((k >> 1) + 1) * Q + ((j >> 1) + 1)) * Q + (h0 + 1);
                 T uv[VEC], res[VEC];
                 ldv<T, VEC>(U + v * VEC, uv);
@@ -621,8 +661,9 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
                     const T *qyz = PS + (2 + 2 * (j & 1) + (k & 1)) * S::N3 + c0;
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) res[e] = fma(T(0.25), px[e] + qyz[e], uv[e]);
-                    (void)oz;
                     (void)b;
+                    (void)ox;
+                    (void)oy;
                 } else {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {

@@ -85,4 +85,72 @@ void launch_leaf_absmax(const LaunchCfg &, const BoxMeta &, const int *list, int
                         double *partials, double *result);
 constexpr int kPartials = 4096;  // size of the partials buffer (doubles)
 
+// Variable-coefficient operators (kernels_var.cuh): op 1 div(eps grad u),
+// op 2 the same in (r,z) coordinates; eps in the field layout, same precision.
+#define AFG_VAR_DECL(DD)                                                                                             \
+    void launch_var_smooth_d##DD(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, const void *rho,        \
+                                 const void *eps, int colour, int hom, int op);                                      \
+    void launch_var_resid_restrict_d##DD(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, void *rho,      \
+                                         void *vold, const void *eps, int hom, int op);                              \
+    void launch_var_fas_d##DD(const LaunchCfg &, const BoxMeta &, int b0, int n, const void *u, void *rho,           \
+                              void *vold, const void *eps, int hom, int op);                                         \
+    void launch_var_restrict_d##DD(const LaunchCfg &, const BoxMeta &, int b0, int n, const int *list, void *v,      \
+                                   int op);                                                                          \
+    void launch_correct_x_d##DD(const LaunchCfg &, const BoxMeta &, int b0, int n, void *u, const void *vold,         \
+                                const int *nball, int scheme);                                                        \
+    void launch_transfer_d##DD(cudaStream_t st, int N, const BoxMeta &Ao, const double *uo, const int *nball_o,      \
+                               const BoxMeta &An, double *un, const int *new_leaves, const int *src,                  \
+                               const int *poff, int n, int scheme);                                                   \
+    void launch_var_leaf_residual_d##DD(const LaunchCfg &, const BoxMeta &, const int *list, int n, const void *u,   \
+                                        const void *rho, const void *eps, int hom, int op, unsigned long long *rmax, \
+                                        unsigned long long *pmax, void *rout, bool rout_f32);
+AFG_VAR_DECL(2)
+AFG_VAR_DECL(3)
+#undef AFG_VAR_DECL
+
+inline void launch_var_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *rho,
+                              const void *eps, int colour, int hom, int op) {
+    if (c.D == 2) launch_var_smooth_d2(c, A, b0, n, u, rho, eps, colour, hom, op);
+    else launch_var_smooth_d3(c, A, b0, n, u, rho, eps, colour, hom, op);
+}
+inline void launch_var_resid_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, void *rho,
+                                      void *vold, const void *eps, int hom, int op) {
+    if (c.D == 2) launch_var_resid_restrict_d2(c, A, b0, n, u, rho, vold, eps, hom, op);
+    else launch_var_resid_restrict_d3(c, A, b0, n, u, rho, vold, eps, hom, op);
+}
+inline void launch_var_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, void *rho, void *vold,
+                           const void *eps, int hom, int op) {
+    if (c.D == 2) launch_var_fas_d2(c, A, b0, n, u, rho, vold, eps, hom, op);
+    else launch_var_fas_d3(c, A, b0, n, u, rho, vold, eps, hom, op);
+}
+// restriction of a field into the parents: the mean of the children (weighted by r when op == 2)
+inline void launch_var_restrict(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *list, void *v,
+                                int op) {
+    if (c.D == 2) launch_var_restrict_d2(c, A, b0, n, list, v, op);
+    else launch_var_restrict_d3(c, A, b0, n, list, v, op);
+}
+// coarse-grid correction with the bi/trilinear (scheme 1) or zeroth-order
+// (scheme 2) prolongation; nball: the same-level neighbour of every box in
+// all 3^D - 1 directions (-1: none)
+inline void launch_correct_x(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold,
+                             const int *nball, int scheme) {
+    if (c.D == 2) launch_correct_x_d2(c, A, b0, n, u, vold, nball, scheme);
+    else launch_correct_x_d3(c, A, b0, n, u, vold, nball, scheme);
+}
+// field transfer after mesh adaptation: new leaf li of the new grid copies
+// old box src[li] (poff[li] < 0) or is prolonged from old leaf src[li] at
+// offset poff[li] (8 bits per axis) with `scheme`
+inline void launch_transfer(int D, cudaStream_t st, int N, const BoxMeta &Ao, const double *uo, const int *nball_o,
+                            const BoxMeta &An, double *un, const int *new_leaves, const int *src, const int *poff,
+                            int n, int scheme) {
+    if (D == 2) launch_transfer_d2(st, N, Ao, uo, nball_o, An, un, new_leaves, src, poff, n, scheme);
+    else launch_transfer_d3(st, N, Ao, uo, nball_o, An, un, new_leaves, src, poff, n, scheme);
+}
+inline void launch_var_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *u,
+                                     const void *rho, const void *eps, int hom, int op, unsigned long long *rmax,
+                                     unsigned long long *pmax, void *rout, bool rout_f32) {
+    if (c.D == 2) launch_var_leaf_residual_d2(c, A, list, n, u, rho, eps, hom, op, rmax, pmax, rout, rout_f32);
+    else launch_var_leaf_residual_d3(c, A, list, n, u, rho, eps, hom, op, rmax, pmax, rout, rout_f32);
+}
+
 }  // namespace afg

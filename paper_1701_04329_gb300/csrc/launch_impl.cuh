@@ -122,7 +122,7 @@ template <int D, int M, int MP, typename T>
 void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     if (n <= 0) return;
     // staged copies; in 3D the pair sums of a coarse cell are shared by its children
-    if constexpr (CpCfg<D, M, T>::ok) {
+    if constexpr (CpCfg<D, M, T>::ok && MP == M) {
         using S = CpCfg<D, M, T>;
         const size_t smem = S::smem();
         auto k = k_correct_p<D, M, MP, T>;

@@ -122,3 +122,24 @@ def test_forest_of_a_block_tree_is_refused():
         except afgpu.AfgError as e:
             assert e.code == afgpu.AFG_ERR_STATE
             assert "several root boxes" in str(e)
+
+
+def test_operator_validated_on_the_host():
+    """afg_set_operator: known operators only, (r,z) in 2D only, single root
+    box; eps needs a variable-coefficient operator first (no GPU needed)."""
+    t = afgpu.Tree(3, 8, 2)
+    for bad in (3, -1, afgpu.AFG_OP_VAR_RZ):
+        try:
+            t.set_operator(bad)
+            assert False, bad
+        except afgpu.AfgError as e:
+            assert e.code == afgpu.AFG_ERR_ARG
+    m = afgpu.Tree(2, 8, 2, roots=(2, 1))
+    try:
+        m.set_operator(afgpu.AFG_OP_VAR)
+        assert False
+    except afgpu.AfgError as e:
+        assert e.code == afgpu.AFG_ERR_ARG
+    L = afgpu.lib()
+    assert L.afg_set_eps(t._h, ctypes.c_void_p(8)) == afgpu.AFG_ERR_STATE
+    afgpu.Tree(2, 8, 2).set_operator(afgpu.AFG_OP_VAR_RZ)
