@@ -87,6 +87,7 @@ typedef struct {
     int bct[6];                      /* per domain side (-x,+x,-y,+y,-z,+z): 0 Dirichlet, 1 Neumann, 2 periodic */
     int op;                          /* 0 Laplacian, 1 div(eps grad), 2 the same in (r,z) with r = x (2D) */
     int prolong;                     /* correction: 0 linear 2-1-1 / 1-1-1-1, 1 bi/trilinear, 2 zeroth order */
+    int singular;                    /* no Dirichlet side: constants are the null space (see make_compatible) */
 } OTree;
 
 /* spatial index q along axis a at a level with `side` boxes per axis: on a
@@ -652,6 +653,60 @@ static void side_cells(int M, int s, int *inner, int *second, int *ghost) {
     else { *inner = M; *second = M - 1; *ghost = M + 1; }
 }
 
+/* Problems without a Dirichlet side (only Neumann and periodic sides) are
+ * singular: constants are the null space of the composite operator, and
+ * A u = rho has a solution only for a compatible source,
+ *   sum_leaves h^D rho = sum_(Neumann leaf faces) h^(D-1) b
+ * (the discrete divergence theorem: the conservative scheme of Sec. 3.3
+ * makes the flux sums cancel between cells).  Sec. 4.4's gravity problem
+ * subtracts the mean source.  Reading: the solver solves A u = rho - c with
+ * c = (sum h^D rho - sum h^(D-1) b) / sum h^D -- the source less its
+ * volume-weighted mean and the boundary inflow per volume (c = 0 for a
+ * compatible source, so the step is idempotent) -- and picks the solution of
+ * zero volume-weighted mean: after every cycle the leaf mean is subtracted
+ * from the leaves.  Only the Laplacian (op 0). */
+static void make_compatible(OTree *t) {
+    if (!t->singular) return;
+    int D = t->D, nc = ipow(t->N, D), nf = ipow(t->N, D - 1);
+    double sr = 0.0, sb = 0.0, sv = 0.0;
+    for (int li = 0; li < t->nleaf; li++) {
+        OMG *m = leaf_mg(t, li);
+        double vol = 1.0, area = 1.0;
+        for (int a = 0; a < D; a++) vol *= m->h;
+        for (int a = 0; a < D - 1; a++) area *= m->h;
+        for (int c = 0; c < nc; c++) sr += vol * m->rho[interior_index(D, m->M, c)];
+        sv += vol * nc;
+        if (t->hom) continue;
+        for (int s = 0; s < 2 * D; s++)
+            if (m->kind[s] == K_PHYS && t->bct[s] == 1)
+                for (int f = 0; f < nf; f++) sb += area * m->bc[s][f];
+    }
+    double c = (sr - sb) / sv;
+    for (int li = 0; li < t->nleaf; li++) {
+        OMG *m = leaf_mg(t, li);
+        for (int q = 0; q < nc; q++) m->rho[interior_index(D, m->M, q)] -= c;
+    }
+}
+
+/* the volume-weighted leaf mean of u, subtracted from the leaves */
+static void remove_mean(OTree *t) {
+    if (!t->singular) return;
+    int D = t->D, nc = ipow(t->N, D);
+    double su = 0.0, sv = 0.0;
+    for (int li = 0; li < t->nleaf; li++) {
+        OMG *m = leaf_mg(t, li);
+        double vol = 1.0;
+        for (int a = 0; a < D; a++) vol *= m->h;
+        for (int c = 0; c < nc; c++) su += vol * m->u[interior_index(D, m->M, c)];
+        sv += vol * nc;
+    }
+    double mean = su / sv;
+    for (int li = 0; li < t->nleaf; li++) {
+        OMG *m = leaf_mg(t, li);
+        for (int c = 0; c < nc; c++) m->u[interior_index(D, m->M, c)] -= mean;
+    }
+}
+
 /* Fill the side ghost cells of variable `which` (0 = u, 1 = d) of all boxes
  * of a level.  Same-level neighbour: copy.  Physical boundary, Dirichlet:
  * g = 2 b - u_1 (reading: b is the value at the face centre; the linear
@@ -1050,12 +1105,17 @@ static void vcycle_from(OTree *t, int ltop, int nd, int nu, int nb) {
     }
 }
 
-void ot_vcycle(OTree *t, int nd, int nu, int nb) { vcycle_from(t, t->L, nd, nu, nb); }
+void ot_vcycle(OTree *t, int nd, int nu, int nb) {
+    make_compatible(t);
+    vcycle_from(t, t->L, nd, nu, nb);
+    remove_mean(t);
+}
 
 /* FMG cycle (Sec. 3.2).  Reading: both start cases are handled by one rule:
  * the current leaf values (zero for a fresh start) are restricted down to
  * the coarsest grid, and Eq. coarse-rhs sets the coarse source terms. */
 void ot_fmg(OTree *t, int nd, int nu, int nb) {
+    make_compatible(t);
     for (int l = t->L; l > t->lmin; l--) restrict_level(t, l, 0);
     for (int l = t->L; l > t->lmin; l--) {
         fill_ghosts(t, l, 0);
@@ -1073,6 +1133,7 @@ void ot_fmg(OTree *t, int nd, int nu, int nb) {
         }
         vcycle_from(t, l, nd, nu, nb);
     }
+    remove_mean(t);
 }
 
 /* Residual norms on the leaves.  Reading: "relative residual" =
@@ -1081,6 +1142,7 @@ void ot_fmg(OTree *t, int nd, int nu, int nb) {
  * sees the mean of the fine cells (the composite operator). */
 void ot_residual_norm(OTree *t, double *rmax, double *rhomax) {
     int D = t->D;
+    make_compatible(t);
     for (int l = t->L; l > 1; l--) restrict_level(t, l, 0);
     for (int l = 1; l <= t->L; l++) fill_ghosts(t, l, 0);
     double rm = 0.0, pm = 0.0;
@@ -1248,6 +1310,7 @@ int ot_set_prolong(OTree *t, int scheme) {
  * of u, so the boundary flux is eps b. */
 int ot_set_operator(OTree *t, int op) {
     if (op < 0 || op > 2 || (op == 2 && t->D != 2)) return -1;
+    if (op && t->singular) return -1;  /* singular problems: the Laplacian only */
     t->op = op;
     return 0;
 }
@@ -1275,7 +1338,7 @@ int ot_set_eps(OTree *t, const double *eps) {
  * to b.  Periodic (Sec. 2.2: the neighbour beyond the last box is the first)
  * applies to both sides of an axis; it changes the connectivity, so it can
  * only be switched on or off while the tree is its root boxes alone.  A tree
- * with no Dirichlet side is singular and is refused. */
+ * with no Dirichlet side is singular (make_compatible). */
 int ot_set_bc_types(OTree *t, const int *types) {
     int any_dirichlet = 0, change = 0;
     for (int s = 0; s < 2 * t->D; s++) {
@@ -1284,9 +1347,10 @@ int ot_set_bc_types(OTree *t, const int *types) {
         any_dirichlet |= types[s] == 0;
         change |= (types[s] == 2) != (t->bct[s] == 2);
     }
-    if (!any_dirichlet) return -1;
     if (change && t->nbox != t->nr[0] * t->nr[1] * t->nr[2]) return -1;
+    if (!any_dirichlet && t->op) return -1;
     for (int s = 0; s < 2 * t->D; s++) t->bct[s] = types[s];
+    t->singular = !any_dirichlet;
     if (change) return rebuild_roots(t);
     return 0;
 }

@@ -160,11 +160,10 @@ def test_neumann_second_order_discretisation_error():
     assert np.all(orders > 1.8), orders
 
 
-def test_all_neumann_is_refused():
-    """Without a Dirichlet side the composite system is singular."""
+def test_invalid_side_types_are_refused():
+    """Periodic sides come in pairs (singular problems without a Dirichlet
+    side are pinned in test_oracle_singular.py)."""
     t = OracleTree(2, 4, 3)
     t.refine_uniform(2)
-    with pytest.raises(ValueError):
-        t.set_boundary_types([1, 1, 1, 1])
     with pytest.raises(ValueError):
         t.set_boundary_types([0, 2, 0, 0])
