@@ -5,11 +5,12 @@
  *
  * Problem (Sec. 3, Eq. mg-discr-equation): A_h(u_h) = rho_h on [0,1]^D, with
  * A the Laplacian or div(eps grad u) (Sec. 3.4-3.5, afg_set_operator),
- * D = 2 or 3, with Dirichlet, Neumann or periodic domain sides (at least one
- * Dirichlet side), discretised on a tree of boxes of N^D cells (Sec. 1.3,
- * 2.1).  A tree's level 1 may be a block of root boxes (domain [0,r_x] x
- * [0,r_y] (x [0,r_z])).  The library holds the tree,
- * its per-level box lists and all field data on the GPU; every operator of
+ * D = 2 or 3, with Dirichlet, Neumann or periodic domain sides (without a
+ * Dirichlet side: the compatible, mean-zero solution), discretised on a
+ * tree of boxes of N^D cells (Sec. 1.3, 2.1).  A tree's level 1 may be a
+ * block of root boxes (domain [0,r_x] x [0,r_y] (x [0,r_z])).  The library
+ * holds the tree, its per-level box lists and all field data on the GPU;
+ * every operator of
  * the solve (ghost cells, red-black Gauss-Seidel, residual, restriction,
  * prolongation, norms) is a CUDA kernel of this library.
  *
@@ -215,9 +216,14 @@ int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *pa
  * both sides of an axis and is a property of the connectivity (Sec. 2.2: the
  * box beyond the last one is the first): those sides carry no boundary faces,
  * and periodicity can only be switched while the tree is its root boxes alone
- * (set it before refining).  At least one side must be Dirichlet (the problem
- * is singular otherwise).  AFG_ERR_ARG for any violation, with the tree
- * unchanged.  Host call; a change discards the device fields, so set rho and
+ * (set it before refining).  Without a Dirichlet side the problem is
+ * singular (constants are the null space): the solver then solves
+ * A u = rho - c, c = (sum h^D rho - sum over Neumann leaf faces h^(D-1) b) /
+ * sum h^D, which makes the source compatible (Sec. 4.4's gravity problem
+ * subtracts the mean source), and returns the solution of zero
+ * volume-weighted mean; such trees work alone (not in forests, not as blocks
+ * of root boxes) with the Laplacian, and have no adjoint.  AFG_ERR_ARG for
+ * any violation, with the tree unchanged.  Host call; a change discards the device fields, so set rho and
  * the boundary data after it.  Default: all sides Dirichlet.  Trees of a
  * forest keep the types they had when the forest was created. */
 #define AFG_BC_DIRICHLET 0

@@ -167,9 +167,11 @@ int solve_fp64(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::v
         for (int t = 0; t < g.T; ++t)
             if (hist[t].empty() || hist[t].back() > o.rel_tol) hist[t].push_back(rel_of(g, t));
     };
+    g.make_compatible(s);
     if (fmg_first) {
         run(g, {1, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) {
             g.fmg(g.ws64, mo, 0, forest, cs);
+            g.remove_mean(g.ws64, cs);
             g.norms_async(g.ws64, 0, nullptr, false, cs);
             g.mask_update_async(cs);
         });
@@ -185,6 +187,7 @@ int solve_fp64(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::v
     while (*g.h_nactive > 0 && cycles < o.max_cycles) {
         run(g, {2, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) {
             g.vcycle(g.ws64, g.lmax, mo, 0, forest ? g.d_converged_mask() : nullptr, cs);
+            g.remove_mean(g.ws64, cs);
             g.norms_async(g.ws64, 0, nullptr, false, cs);
             g.mask_update_async(cs);
         });
@@ -213,6 +216,7 @@ int solve_mixed(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::
             if (hist[t].empty() || hist[t].back() > o.rel_tol) hist[t].push_back(rel_of(g, t));
     };
     const size_t bytes32 = (size_t)g.ncell * 4;
+    g.make_compatible(s);
     auto residual = [&](cudaStream_t cs) {
         g.norms_async(g.ws64, 0, g.ws32.rho->p, true, cs);
         g.mask_update_async(cs);
@@ -233,6 +237,7 @@ int solve_mixed(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::
                 A.active = active;
                 afg::launch_mixed_update(g.leaf_cfg(true, cs), A, g.d_leaves, g.n_leaf_boxes, g.ws64.u->as<double>(),
                                          g.ws32.u->as<float>());
+                g.remove_mean(g.ws64, cs);
                 residual(cs);
             });
         check(cudaStreamSynchronize(s), "solve");
@@ -561,6 +566,11 @@ int afg_flag_cells(afg_tree *t, const double *f_dev, int power, double tau_refin
 
 int afg_set_boundary_types(afg_tree *t, const int *types) {
     if (!t || !types) return fail(AFG_ERR_ARG, "null argument");
+    if (t->op) {
+        bool dir = false;
+        for (int s2 = 0; s2 < 2 * t->ht.D; ++s2) dir |= types[s2] == 0;
+        if (!dir) return fail(AFG_ERR_ARG, "the variable-coefficient operators need a Dirichlet side");
+    }
     AFG_API_BEGIN
     std::string err;  // a change rebuilds the host tree (new version: the device grid follows)
     if (t->ht.set_boundary_types(types, err)) return fail(AFG_ERR_ARG, err);
@@ -626,6 +636,9 @@ int afg_set_operator(afg_tree *t, int op) {
     if (op == 2 && t->ht.D != 2) return fail(AFG_ERR_ARG, "(r,z) coordinates need a 2D tree");
     if (op && t->ht.nroots() != 1) return fail(AFG_ERR_ARG, "the variable-coefficient operators need a single root box");
     if (op == 2 && t->ht.bct[0] == 2) return fail(AFG_ERR_ARG, "(r,z): the -x side is the axis and cannot be periodic");
+    bool dir = false;
+    for (int s2 = 0; s2 < 2 * t->ht.D; ++s2) dir |= t->ht.bct[s2] == 0;
+    if (op && !dir) return fail(AFG_ERR_ARG, "the variable-coefficient operators need a Dirichlet side");
     AFG_API_BEGIN
     t->op = op;
     if (t->grid) {  // the device data stays; the cycles change (graphs are recaptured) and eps is needed again
@@ -720,9 +733,11 @@ static int one_cycle(afg_tree *t, const afg_mg_opts *opts, afg_stats *st, bool f
     if (int rc = ready(g)) return rc;
     const auto t0 = clk::now();
     const afg::MgOpts mo{o.n_down, o.n_up, o.n_base};
+    g.make_compatible(t->stream);
     run(g, {fmg ? 30 : 31, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, t->stream, [&](cudaStream_t cs) {
         if (fmg) g.fmg(g.ws64, mo, 0, false, cs);
         else g.vcycle(g.ws64, g.lmax, mo, 0, nullptr, cs);
+        g.remove_mean(g.ws64, cs);
         g.norms_async(g.ws64, 0, nullptr, false, cs);
     });
     check(cudaStreamSynchronize(t->stream), "cycle");
@@ -767,6 +782,7 @@ int afg_residual_norm(afg_tree *t, double *max_abs_r, double *max_abs_rho) {
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     if (g.op && !g.eps_set) return fail(AFG_ERR_STATE, "the variable-coefficient operator needs eps (afg_set_eps)");
+    if (g.rhs_set) g.make_compatible(t->stream);
     g.norms_async(g.ws64, 0, nullptr, false, t->stream);
     check(cudaStreamSynchronize(t->stream), "residual norm");
     if (max_abs_r) *max_abs_r = as_double(g.h_norms[0]);
@@ -784,6 +800,7 @@ int afg_adjoint(afg_tree *t, const double *g_leaf, double *lambda_leaf, double *
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     if (g.op) return fail(AFG_ERR_STATE, "the adjoint is built for the Laplacian only");
+    if (g.singular) return fail(AFG_ERR_STATE, "the adjoint needs a Dirichlet side");
     const auto t0 = clk::now();
     double rel = 0.0;
     const int its = adjoint_solve(g, o, t->stream, g_leaf, &rel);

@@ -93,6 +93,13 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     N = trees[0]->N;
     T = (int)trees.size();
     block = trees[0]->nroots() != 1;
+    for (const HostTree *h : trees) {
+        bool dir = false;
+        for (int s2 = 0; s2 < 2 * D; ++s2) dir |= h->bct[s2] == 0;
+        singular |= !dir;
+    }
+    if (singular && (T > 1 || block))
+        throw std::runtime_error("problems without a Dirichlet side are solved for single trees of one root box");
     if (block) {
         const size_t need = bottom_block_smem(trees[0]->D, true, trees[0]->N, trees[0]->nr, trees[0]->bct);
         if (need > max_smem_optin())
@@ -197,6 +204,20 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
                 if (hx.nb[d] >= 0) nball[(size_t)g * NDIR + d] = gid[t][hx.nb[d]];
             for (int c = 0; c < NC; ++c) child[g * NC + c] = hx.child[c] >= 0 ? gid[t][hx.child[c]] : -1;
         }
+    }
+    // sibling groups: on every level from 2 up the boxes of a parent are
+    // consecutive (Morton order) with child c at offset bit a = (c >> a) & 1
+    for (auto &v : lv) {
+        if (v.l < 2 || v.nb % NC) continue;
+        bool ok = true;
+        for (int q = 0; ok && q < v.nb / NC; ++q)
+            for (int c = 0; ok && c < NC; ++c) {
+                const int g = v.b0 + NC * q + c;
+                int want = 0;
+                for (int a = 0; a < D; ++a) want |= (((c >> a) & 1) * (N / 2)) << (8 * a);
+                ok = parent[g] == parent[v.b0 + NC * q] && poff[g] == want;
+            }
+        v.sibs = ok;
     }
     // Dirichlet storage: leaf faces first, in canonical (tree-major) order, so
     // that user face arrays map onto it directly; then the coarse boxes' faces.
@@ -493,6 +514,19 @@ void Grid::fmg_low_levels(Workspace &w, const MgOpts &o, int hom, cudaStream_t s
         if (l > lmin) correct(w, l, nullptr, s);
         vcycle_levels(w, l, o, hom, nullptr, s);
     }
+}
+
+// Problems without a Dirichlet side: A u = rho - c with c the volume-weighted
+// mean of rho less the Neumann inflow per volume (idempotent: c = 0 for a
+// compatible source), and the solution of zero volume-weighted mean.
+void Grid::make_compatible(cudaStream_t s) {
+    if (!singular) return;
+    launch_leaf_center(*this, ws64.rho->as<double>(), true, s);
+    leaf_rho_hat(ws64, s);
+}
+
+void Grid::remove_mean(Workspace &w, cudaStream_t s) {
+    if (singular && w.fp64) launch_leaf_center(*this, w.u->as<double>(), false, s);
 }
 
 // eps on the leaves, restricted to every parent (level by level, finest

@@ -84,6 +84,7 @@ class Grid {
         int *d_leaves = nullptr;
         int nleaves = 0;
         long long c0 = 0, ncell = 0;  // cell range of the level
+        bool sibs = false;            // boxes in sibling groups (checked when the grid is built)
     };
 
     int D, N, T, lmin, lmax;
@@ -129,6 +130,11 @@ class Grid {
     // variable coefficients or another prolongation: every level on the per-level kernels
     bool levels_path() const { return op != 0 || prolong != 0; }
     void correct(Workspace &w, int l, const int *active, cudaStream_t s);
+    // no Dirichlet side (single trees): the source is made compatible and the
+    // solution kept at zero volume-weighted mean
+    bool singular = false;
+    void make_compatible(cudaStream_t s);
+    void remove_mean(Workspace &w, cudaStream_t s);
     const void *eps_of(const Workspace &w) const { return w.fp64 ? eps64->p : eps32->p; }
     void set_eps(const double *eps_leaf, cudaStream_t s);
     std::vector<std::unique_ptr<DevBuf>> bicg;  // adjoint vectors
@@ -136,7 +142,7 @@ class Grid {
 
     LaunchCfg cfg(int l, bool fp64, cudaStream_t s) {
         auto &v = L(l);
-        return LaunchCfg{s, D, v.M, v.MP, fp64};
+        return LaunchCfg{s, D, v.M, v.MP, fp64, v.sibs};
     }
     LaunchCfg leaf_cfg(bool fp64, cudaStream_t s) const { return LaunchCfg{s, D, N, N / 2, fp64}; }
 
@@ -178,6 +184,8 @@ void launch_cell_centers(const Grid &g, double *xyz, cudaStream_t s);
 // refinement flags of the leaf cells from a leaf field (canonical order)
 void launch_flag(const Grid &g, const double *f, int power, double tau_ref, double tau_de, signed char *flags,
                  cudaStream_t s);
+// f -= (sum_leaves h^D f - [sum over Neumann leaf faces h^(D-1) b]) / sum h^D on the leaves
+void launch_leaf_center(const Grid &g, double *f, bool with_flux, cudaStream_t s);
 // dst = (float) src, n values
 void launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
 

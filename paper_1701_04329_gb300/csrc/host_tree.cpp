@@ -93,7 +93,7 @@ int HostTree::set_boundary_types(const int *types, std::string &err) {
         any_dirichlet |= types[s] == 0;
         change |= (types[s] == 2) != (bct[s] == 2);
     }
-    if (!any_dirichlet) { err = "at least one side must be Dirichlet (the problem is singular otherwise)"; return -1; }
+    (void)any_dirichlet;  // without a Dirichlet side the problem is singular; the solver handles it
     if (change && (int)boxes.size() != nroots()) { err = "periodic sides can only be switched while the tree is its root boxes"; return -1; }
     bool same = true;
     for (int s = 0; s < 2 * D; ++s) same &= bct[s] == types[s];

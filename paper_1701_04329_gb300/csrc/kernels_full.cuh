@@ -678,4 +678,174 @@ __global__ void __launch_bounds__(kThreads) k_correct_p(BoxMeta A, int b0, int n
     cp_wait<0>();
 }
 
+// Coarse-grid correction by parent: the 2^D children of a parent are
+// consecutive in a level's box range, so one CTA stages the parent P once --
+// its u and v' images with their side ghosts, as the whole-box kernels stage
+// a box (fp_issue; across a domain side the mirrored inner value) -- forms
+// d = v_H - v'_H on the image (negated across a Dirichlet side, the
+// homogeneous rule of the correction), in 3D the pair sums of every parent
+// cell, and updates all children's cells with the 2-1-1 / 1-1-1-1 scheme
+// (the same arithmetic as k_correct_p).  Parents are staged one ahead
+// (two-stage ring).
+template <int D, int M, typename T>
+struct PpCfg {
+    using F = FpCfg<D, M, T, kThreads>;
+    static constexpr int NC = 1 << D, C = Geo<D, M>::C, VEC = F::VEC, NV = C / VEC;
+    static constexpr int IMG = F::UB;                  // one image (u or v') with its ghosts
+    static constexpr int PSZ = D == 3 ? 6 * C : 0;     // pair sums of the parent's cells
+    static constexpr int NST = 2;
+    static constexpr size_t smem() {
+        return sizeof(T) * (2 * IMG * NST + PSZ) + sizeof(BoxInfo) * (NST + 1) + sizeof(long long) * NC * (NST + 1);
+    }
+    static constexpr bool ok = F::ok;
+};
+
+// metadata of parent group q: the parent of boxes b0 + NC q .. b0 + NC q + NC - 1
+// and its children's cell offsets
+template <int D, int M, typename T>
+__device__ __forceinline__ void pp_info_load(const BoxMeta &A, int q, int np, int b0, BoxInfo &I, long long *ccoff,
+                                             bool mask) {
+    using S = PpCfg<D, M, T>;
+    const int lt = threadIdx.x;
+    const int b = q < np ? A.parent[b0 + S::NC * q] : -1;
+    bool on = b >= 0;
+    if (on && mask && A.active && !A.active[A.tree[b]]) on = false;
+    if (lt < 2 * D) {
+        if (on) {
+            I.code[lt] = A.nb[b * 2 * D + lt];
+            I.base[lt] = A.nbase[b * 2 * D + lt];
+        }
+    } else if (lt == 2 * D) {
+        I.b = on ? b : -1;
+        if (on) {
+            I.coff = A.coff[b];
+            I.flag = A.bflag[b];
+            I.nmask = I.flag >> BF_NSHIFT;
+        }
+    } else if (lt >= 32 && lt < 32 + S::NC) {
+        if (on) ccoff[lt - 32] = A.coff[b0 + S::NC * q + (lt - 32)];
+    }
+}
+
+template <int D, int M, typename T>
+__global__ void __launch_bounds__(kThreads) k_correct_pp(BoxMeta A, int b0, int n, T *u, const T *__restrict__ vold) {
+    using S = PpCfg<D, M, T>;
+    using F = typename S::F;
+    constexpr int NST = S::NST, NI = NST + 1, MH = M / 2, VEC = S::VEC, NVH = Geo<D, M>::H / VEC, NVR = F::NVR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *stages = reinterpret_cast<T *>(smem_raw);
+    T *PS = stages + 2 * S::IMG * NST;
+    BoxInfo *info = reinterpret_cast<BoxInfo *>(smem_raw + sizeof(T) * (2 * S::IMG * NST + S::PSZ));
+    long long *ccoff = reinterpret_cast<long long *>(info + NI);
+    const int lt = threadIdx.x;
+    const int np = n / S::NC;
+    pdl_trigger();
+    for (int q = 0; q < NST; ++q)  // static metadata: before the wait
+        pp_info_load<D, M, T>(A, blockIdx.x + q * gridDim.x, np, b0, info[q], ccoff + q * S::NC, false);
+    pdl_wait();
+    __syncthreads();
+    if (lt == 2 * D)
+        for (int q = 0; q < NST; ++q)
+            if (info[q].b >= 0 && A.active && !A.active[A.tree[info[q].b]]) info[q].b = -1;
+    __syncthreads();
+    auto issue = [&](int q) {
+        const BoxInfo &In = info[q % NI];
+        if (In.b >= 0) {
+            T *st = stages + (q % NST) * 2 * S::IMG;
+            fp_issue<D, M, T, kThreads>(In, u, nullptr, st, lt, true);
+            fp_issue<D, M, T, kThreads>(In, vold, nullptr, st + S::IMG, lt, true);
+        }
+        cp_commit();
+    };
+    for (int q = 0; q < NST - 1; ++q) issue(q);
+    int it = 0;
+    for (int base = blockIdx.x; base < np; base += gridDim.x, ++it) {
+        cp_wait<NST - 2>();
+        __syncthreads();  // the parent's images have landed; the previous stage and slots are free
+        const BoxInfo &I = info[it % NI];
+        const long long *cc = ccoff + (it % NI) * S::NC;
+        T *Dd = stages + (it % NST) * 2 * S::IMG;
+        const T *V = Dd + S::IMG;
+        issue(it + NST - 1);
+        pp_info_load<D, M, T>(A, base + NST * gridDim.x, np, b0, info[(it + NST) % NI], ccoff + ((it + NST) % NI) * S::NC,
+                              true);
+        const bool on = I.b >= 0;
+        if (on)
+            for (int e = lt; e < S::IMG; e += kThreads) Dd[e] = Dd[e] - V[e];
+        if (on && (I.flag & BF_SPECIAL)) {  // a Dirichlet side: the difference enters as -d
+            __syncthreads();
+            for (int item = lt; item < F::NGI; item += kThreads) {
+                int sd, slot;
+                if (item < F::NXI) {
+                    int j, k;
+                    fp_xitem<D, M>(item, sd, j, k);
+                    slot = 2 * F::PT + sd * F::ROWS + sp_row<D, M>(j, k);
+                    if (I.code[sd] == -1 && !((I.nmask >> sd) & 1)) Dd[slot] = -Dd[slot];
+                } else {
+                    int col, h0, jg, kg, jin, kin, jm, km;
+                    fp_yzitem<D, M, T>(item - F::NXI, sd, col, h0, jg, kg, jin, kin, jm, km);
+                    slot = col * F::PT + sp_row<D, M>(jg, kg) * MH + h0;
+                    if (I.code[sd] == -1 && !((I.nmask >> sd) & 1))
+#pragma unroll
+                        for (int x = 0; x < VEC; ++x) Dd[slot + x] = -Dd[slot + x];
+                }
+            }
+        }
+        __syncthreads();
+        // d of parent cell (i, j, k), i in [-1, M]: the planes, or the x ghosts
+        auto dat = [&](int i, int j, int k) -> T {
+            if (i < 0) return Dd[2 * F::PT + sp_row<D, M>(j, k)];
+            if (i >= M) return Dd[2 * F::PT + F::ROWS + sp_row<D, M>(j, k)];
+            return Dd[fp_slot<D, M, T>(i, j, k)];
+        };
+        if constexpr (D == 3) {
+            if (on)
+                for (int c = lt; c < S::C; c += kThreads) {
+                    const int X = c % M, Y = (c / M) % M, Z = c / (M * M);
+                    const T d0 = dat(X, Y, Z), dym = dat(X, Y - 1, Z), dyp = dat(X, Y + 1, Z);
+                    const T dzm = dat(X, Y, Z - 1), dzp = dat(X, Y, Z + 1);
+                    PS[c] = d0 + dat(X - 1, Y, Z);
+                    PS[S::C + c] = d0 + dat(X + 1, Y, Z);
+                    PS[2 * S::C + c] = dym + dzm;
+                    PS[3 * S::C + c] = dym + dzp;
+                    PS[4 * S::C + c] = dyp + dzm;
+                    PS[5 * S::C + c] = dyp + dzp;
+                }
+            __syncthreads();
+        }
+        if (on) {
+            for (int t = lt; t < S::NC * S::NV; t += kThreads) {
+                const int ch = t / S::NV, v = t % S::NV;
+                // the child's offset in the parent: bit a of ch is its half along axis a
+                const int px = (ch & 1) * MH, py = ((ch >> 1) & 1) * MH, pz = D == 3 ? ((ch >> 2) & 1) * MH : 0;
+                const int col = v / NVH, w = v % NVH;
+                const int row = w / NVR, h0 = (w % NVR) * VEC;
+                const int j = row % M, k = D == 2 ? 0 : row / M;
+                const int r = (col + j + k + D) & 1;
+                T uv[VEC], res[VEC];
+                T *gu = u + cc[ch] + (long long)v * VEC;
+                ldv<T, VEC>(gu, uv);
+                const int Y = py + (j >> 1), Z = pz + (k >> 1), X0 = px + h0;
+                if constexpr (D == 3) {
+                    const int c0 = (Z * M + Y) * M + X0;
+                    const T *pxs = PS + (r ? S::C : 0) + c0;
+                    const T *qyz = PS + (2 + 2 * (j & 1) + (k & 1)) * S::C + c0;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) res[e] = fma(T(0.25), pxs[e] + qyz[e], uv[e]);
+                } else {
+                    const int sy = (j & 1) ? 1 : -1, sx = r ? 1 : -1;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const int X = X0 + e;
+                        const T d0 = dat(X, Y, 0), dx = dat(X + sx, Y, 0), dy = dat(X, Y + sy, 0);
+                        res[e] = fma(T(0.25), dx + dy, fma(T(0.5), d0, uv[e]));
+                    }
+                }
+                stv<T, VEC>(gu, res);
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
 }  // namespace afg

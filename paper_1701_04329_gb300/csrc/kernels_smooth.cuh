@@ -283,6 +283,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
     const int first = blockIdx.x * S::BPC;
     SpPlan<D, M, T> pl;
     pl.init(lt, c);
+    // per vector of this thread, the same for every box: the stage offset of
+    // the x neighbour past the vector (half-row or x ghost) and the parity of
+    // its row (the vector's own half-row is at pl.vdst)
+    int cxoff[S::NIT];
+    bool cr[S::NIT];
+#pragma unroll
+    for (int itv = 0; itv < S::NIT; ++itv) {
+        const int v = lt + itv * S::G;
+        const int row = v / S::NVR, h0 = (v % S::NVR) * VEC;
+        const int j = row % M, k = D == 2 ? 0 : row / M;
+        const int r = (c + j + k + D) & 1;
+        const int pr_row = sp_row<D, M>(j, k);
+        if (r) cxoff[itv] = h0 + VEC < MH ? pr_row * MH + h0 + VEC : S::PT + S::ROWS + pr_row;
+        else cxoff[itv] = h0 > 0 ? pr_row * MH + h0 - 1 : S::PT + pr_row;
+        cr[itv] = r;
+    }
     pdl_trigger();
     for (int q = 0; q < NST; ++q)  // static metadata: before the wait
         info_load<D>(A, first + q * stride + g, n, b0, list, info[q * S::BPC + g], lt, S::G, false);
@@ -315,37 +331,32 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
             __syncthreads();
         }
         if (b >= 0) {
-            const T *P = box, *X = box + S::PT, *R = box + S::PT + S::XT;
+            const T *R = box + S::PT + S::XT;
 #pragma unroll
             for (int itv = 0; itv < S::NIT; ++itv) {
-                const int v = lt + itv * S::G;
-                if (v >= S::NV) continue;
-                const int row = v / S::NVR, h0 = (v % S::NVR) * VEC;
-                const int j = row % M, k = D == 2 ? 0 : row / M;
-                const int r = (c + j + k + D) & 1;
-                const int pr_row = sp_row<D, M>(j, k);
-                const T *pr = P + pr_row * MH + h0;
+                if (lt + itv * S::G >= S::NV) continue;
+                const T *pr = box + pl.vdst[itv];  // the vector's colour 1-c half-row
                 T xv[VEC], ym[VEC], yp[VEC], zm[VEC], zp[VEC], rv[VEC];
                 ldv<T, VEC>(pr, xv);
-                T extra;
-                if (r) extra = h0 + VEC < MH ? pr[VEC] : X[S::ROWS + pr_row];
-                else extra = h0 > 0 ? pr[-1] : X[pr_row];
+                const T extra = box[cxoff[itv]];
                 ldv<T, VEC>(pr - MH, ym);
                 ldv<T, VEC>(pr + MH, yp);
                 if (D == 3) {
                     ldv<T, VEC>(pr - (M + 2) * MH, zm);
                     ldv<T, VEC>(pr + (M + 2) * MH, zp);
                 }
-                ldv<T, VEC>(R + v * VEC, rv);
+                ldv<T, VEC>(R + (lt + itv * S::G) * VEC, rv);
+                const bool r = cr[itv];
                 T out[VEC];
 #pragma unroll
                 for (int x = 0; x < VEC; ++x) {
-                    const T xl = r ? xv[x] : (x ? xv[x - 1] : extra);
-                    const T xr = r ? (x + 1 < VEC ? xv[x + 1] : extra) : xv[x];
-                    const T sum = nb_sum6<D, T>(xl, xr, ym[x], yp[x], D == 3 ? zm[x] : T(0), D == 3 ? zp[x] : T(0));
+                    // the x neighbours: the cell's own half-row entry and the one beside it
+                    // (towards +x for r = 1, towards -x for r = 0; `extra` past the vector)
+                    const T side = r ? (x + 1 < VEC ? xv[x + 1] : extra) : (x ? xv[x - 1] : extra);
+                    const T sum = nb_sum6<D, T>(xv[x], side, ym[x], yp[x], D == 3 ? zm[x] : T(0), D == 3 ? zp[x] : T(0));
                     out[x] = scaled ? fma(sum, inv, rv[x]) : (sum - h2 * rv[x]) * inv;
                 }
-                stv<T, VEC>(u + I.coff + c * H + v * VEC, out);
+                stv<T, VEC>(u + I.coff + c * H + (lt + itv * S::G) * VEC, out);
             }
         }
     }

@@ -14,6 +14,9 @@ struct LaunchCfg {
     int M;      // cells per box side on this level
     int MP;     // cells per box side on the parent level (M or M/2)
     bool fp64;  // double (true) or float (false) field data
+    // the boxes of the range come in sibling groups: 2^D consecutive boxes
+    // share a parent, child c of a group at offset bit a = (c >> a) & 1
+    bool sibs = false;
 };
 
 // counts launches of this library's kernels (host side)

@@ -121,6 +121,17 @@ void do_fas(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const void *u, 
 template <int D, int M, int MP, typename T>
 void do_correct(const LaunchCfg &c, const BoxMeta &A, int b0, int n, void *u, const void *vold) {
     if (n <= 0) return;
+    // one CTA per parent: the parent staged once for its 2^D children
+    if constexpr (PpCfg<D, M, T>::ok && MP == M) {
+        if (c.sibs) {
+            using S = PpCfg<D, M, T>;
+            const size_t smem = S::smem();
+            auto k = k_correct_pp<D, M, T>;
+            launch_pdl(k, grid_for(k, smem, n / S::NC), smem, c.stream, A, b0, n, (T *)u, (const T *)vold);
+            ++g_launches;
+            return;
+        }
+    }
     // staged copies; in 3D the pair sums of a coarse cell are shared by its children
     if constexpr (CpCfg<D, M, T>::ok && MP == M) {
         using S = CpCfg<D, M, T>;

@@ -36,6 +36,7 @@ extern "C" int afg_forest_residual_norms_noalloc(afg_forest *f, double *max_abs_
         return noalloc_fail(AFG_ERR_ARG, "forest has more trees than the 1024 the allocation-free norm supports");
     if (!g.rhs_set) return noalloc_fail(AFG_ERR_STATE, "no right-hand side set");
     if (g.op) return noalloc_fail(AFG_ERR_STATE, "the allocation-free norm covers the Laplacian only");
+    if (g.singular) return noalloc_fail(AFG_ERR_STATE, "the allocation-free norm needs a Dirichlet side");
     // the forest's device (where its data and this call's kernels live)
     const int dev = f->device;
     int prev = -1;

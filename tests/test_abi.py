@@ -61,12 +61,13 @@ def test_errors_are_status_codes():
 
 
 def test_boundary_types_validated_on_the_host():
-    """afg_set_boundary_types: 0/1 per side, at least one Dirichlet side;
-    a refused call leaves the types (and the tree) unchanged."""
+    """afg_set_boundary_types: 0/1/2 per side, periodic sides in pairs; a
+    refused call leaves the types (and the tree) unchanged.  Only Neumann
+    sides (a singular problem) are accepted."""
     import numpy as np
     t = afgpu.Tree(2, 8, 4)
     t.refine_uniform(2)
-    for bad in ([1, 1, 1, 1], [0, 2, 0, 0], [0, -1, 0, 0]):
+    for bad in ([0, 2, 0, 0], [0, -1, 0, 0], [3, 0, 0, 0]):
         try:
             t.set_boundary_types(bad)
             assert False, bad
@@ -74,6 +75,13 @@ def test_boundary_types_validated_on_the_host():
             assert e.code == afgpu.AFG_ERR_ARG
     t.set_boundary_types([afgpu.AFG_BC_NEUMANN, afgpu.AFG_BC_DIRICHLET, afgpu.AFG_BC_NEUMANN, afgpu.AFG_BC_DIRICHLET])
     assert t.info().n_boxes == 5
+    t.set_boundary_types([afgpu.AFG_BC_NEUMANN] * 4)
+    t.set_operator(afgpu.AFG_OP_LAPLACE)
+    try:  # the variable-coefficient operators need a Dirichlet side
+        t.set_operator(afgpu.AFG_OP_VAR)
+        assert False
+    except afgpu.AfgError as e:
+        assert e.code == afgpu.AFG_ERR_ARG
     try:
         t.set_boundary_types([1, 0, 1])  # wrong count for 2D
         assert False
@@ -84,7 +92,7 @@ def test_boundary_types_validated_on_the_host():
 def test_periodic_types_validated_on_the_host():
     """Periodic sides come in pairs and switch only on the root box alone."""
     t = afgpu.Tree(3, 8, 4)
-    for bad in ([2, 0, 0, 0, 0, 0], [2, 2, 2, 2, 2, 2], [2, 2, 1, 1, 2, 2]):
+    for bad in ([2, 0, 0, 0, 0, 0], [2, 1, 0, 0, 0, 0], [0, 0, 0, 0, 1, 2]):
         try:
             t.set_boundary_types(bad)
             assert False, bad
