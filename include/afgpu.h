@@ -130,16 +130,19 @@ int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out);
  * ints, each in [1, 64]) root boxes per axis, each the unit square/cube, so
  * the domain is [0,nroot[0]] x [0,nroot[1]] (x [0,nroot[2]]).  Root boxes
  * come first in the canonical box order (Morton order of their indices).
- * Every call accepts such trees: below level 1 the coarse grids hold one box
- * per root, solved together in one CTA (Sec. 3.2), so level 1 and those
- * grids must fit one CTA's shared memory (227 KB on GB300): per grid of M =
- * 2, 4, ..., N cells per root, 4 FP64 arrays of (r_x M + 2)(r_y M + 2)
- * (x (r_z M + 2)) values plus the face data of the non-periodic sides.  That takes up to 8 x 8 roots of 8^2 boxes (2D), 4 x 4
- * of 16^2 boxes, 6 x 1 x 1 or 3 x 2 x 1 roots of 8^3 boxes (a 2 x 2 x 2 block
- * of 8^3 boxes is refused) and no block of 16^3 boxes.  A larger block fails
- * with AFG_ERR_STATE at its first field call (afg_set_rhs and the like), when
- * the device grid is built.  Forests of such trees, of any size, are refused
- * (AFG_ERR_STATE).  AFG_ERR_ARG when nroot[a] << (max_level-1) exceeds 2^21. */
+ * Every call accepts such trees: below level 1 the coarse grids of N/2, ...,
+ * 2 cells hold one box per root, connected like the roots (Sec. 3.2: the
+ * coarsest grid holds several boxes, relaxed together).  A single tree whose
+ * block fits one CTA's shared memory (227 KB on GB300: per grid of M = 2, 4,
+ * ..., N cells per root, 4 FP64 arrays of (r_x M + 2)(r_y M + 2)
+ * (x (r_z M + 2)) values plus the face data of the non-periodic sides -- up
+ * to 8 x 8 roots of 8^2 boxes, 4 x 4 of 16^2, 6 x 1 x 1 or 3 x 2 x 1 of 8^3,
+ * no block of 16^3 boxes) solves them in that CTA, one launch per cycle;
+ * larger blocks, and every tree of a forest that holds a block tree, run
+ * them as device boxes through the per-level kernels, like the finer levels.
+ * The variable-coefficient operators and the other prolongations take trees
+ * of one root box (AFG_ERR_ARG); singular problems too.  AFG_ERR_ARG when
+ * nroot[a] << (max_level-1) exceeds 2^21. */
 int afg_tree_create_roots(int dim, int box_n, int max_level, const int *nroot, afg_tree **out);
 int afg_tree_destroy(afg_tree *t);
 
@@ -378,7 +381,8 @@ int afg_kernel_launches(unsigned long long *count);
 /* Times one kernel of the solve on its own, with CUDA events on the tree's
  * stream: `reps` launches on every box of `level` (after one warm-up launch),
  * in FP64 (fp64 = 1) or FP32.  kernel: 0 = red-black half-sweep (Sec. 3.1,
- * colours alternating), 1 = fused residual + restriction (level >= 2),
+ * colours alternating; the FP32 one with homogeneous boundary data, as the
+ * mixed-precision solve runs it), 1 = fused residual + restriction (level >= 2),
  * 2 = prolongation + correction (level >= 2), 3 = leaf residual with its
  * max-norm reduction (all leaves; `level` ignored), 4 = FP64 FMA issue-rate
  * probe (independent FMA chains; `level` ignored; flops count an FMA as 2;

@@ -828,8 +828,6 @@ int afg_forest_create(int n, afg_tree *const *trees, afg_forest **out) {
         if (!trees[i] || trees[i]->ht.D != trees[0]->ht.D || trees[i]->ht.N != trees[0]->ht.N)
             return fail(AFG_ERR_ARG, "trees must exist and share dim and box_n");
     for (int i = 0; i < n; ++i) {
-        if (trees[i]->ht.nroots() != 1)
-            return fail(AFG_ERR_STATE, "a forest cannot hold trees of several root boxes");
         if (trees[i]->op != trees[0]->op || trees[i]->prolong != trees[0]->prolong)
             return fail(AFG_ERR_ARG, "the trees of a forest must share the operator and the prolongation");
     }
@@ -961,8 +959,9 @@ int time_kernel_on(Grid &g, cudaStream_t s, int kernel, int level, int fp64, int
     auto launch = [&](int i) {
         if (kernel == 0) {
             auto &v = g.L(level);
+            // FP32 half-sweeps run with homogeneous boundary data, as in the mixed-precision solve
             afg::launch_smooth(g.cfg(level, fp64, s), g.meta, v.b0, v.nb, nullptr, w.u->p, w.rho->p, w.rhoh_p(), v.h * v.h,
-                               i & 1, 0);
+                               i & 1, fp64 ? 0 : 1);
         } else if (kernel == 1) {
             auto &v = g.L(level);
             afg::launch_resid_restrict(g.cfg(level, fp64, s), g.meta, v.b0, v.nb, w.u->p, w.rho->p, w.vold->p,

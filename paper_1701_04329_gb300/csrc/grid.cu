@@ -82,31 +82,28 @@ T *upload(const std::vector<T> &v, std::vector<std::unique_ptr<DevBuf>> &owned) 
 
 Grid::Grid(const std::vector<const HostTree *> &trees) {
     device = current_device();
-    // the device hierarchy below level 1 holds one box per tree (the root's
-    // coarse grids, solved in one block); a block of several root boxes needs
-    // coarse levels of several connected boxes, which the device path lacks
-    for (const HostTree *h : trees)
-        if (h->nroots() != 1 && trees.size() > 1)
-            throw std::runtime_error("a forest cannot hold trees of several root boxes");
-    // (afg_forest_create refuses such trees in a forest of any size)
     D = trees[0]->D;
     N = trees[0]->N;
     T = (int)trees.size();
-    block = trees[0]->nroots() != 1;
+    // Below level 1 every root box has its coarse grids of N/2, ..., 2 cells
+    // (Sec. 3.2), connected like the roots.  A single tree whose level 1 is a
+    // block of root boxes small enough for one CTA's shared memory keeps them
+    // there only (k_bottom_block); otherwise they are device boxes, one per
+    // root and level, and the cycle runs on the per-level kernels down to the
+    // coarsest grid (several roots: `roots_levels`), or, with one root per
+    // tree, in one launch per cycle (k_bottom).
+    bool multi = false;
+    for (const HostTree *h : trees) multi |= h->nroots() != 1;
+    block = T == 1 && multi &&
+            bottom_block_smem(D, true, N, trees[0]->nr, trees[0]->bct) <= max_smem_optin();
+    roots_levels = multi && !block;
     for (const HostTree *h : trees) {
         bool dir = false;
         for (int s2 = 0; s2 < 2 * D; ++s2) dir |= h->bct[s2] == 0;
         singular |= !dir;
     }
-    if (singular && (T > 1 || block))
+    if (singular && (T > 1 || multi))
         throw std::runtime_error("problems without a Dirichlet side are solved for single trees of one root box");
-    if (block) {
-        const size_t need = bottom_block_smem(trees[0]->D, true, trees[0]->N, trees[0]->nr, trees[0]->bct);
-        if (need > max_smem_optin())
-            throw std::runtime_error("the block of root boxes is too large for the one-CTA bottom solve (" +
-                                     std::to_string(need) + " bytes of shared memory, " +
-                                     std::to_string(max_smem_optin()) + " available)");
-    }
     int nsub = 0;
     if (!block)
         for (int m = N / 2; m >= 2; m /= 2) ++nsub;
@@ -134,7 +131,11 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
         cells = (cells + 63) / 64 * 64;  // 64-cell alignment keeps every box 16-byte aligned for vector loads
         v.c0 = cells;
         for (int t = 0; t < T; ++t) {
-            if (l <= 0) { sub[t][l - lmin] = next++; continue; }
+            if (l <= 0) {  // one box per root box of the tree, in the roots' order
+                sub[t][l - lmin] = next;
+                next += trees[t]->nroots();
+                continue;
+            }
             const HostTree &ht = *trees[t];
             if (l > ht.L) continue;
             for (int b = ht.lstart[l]; b < ht.lstart[l] + ht.lcount[l]; ++b) gid[t][b] = next++;
@@ -163,24 +164,30 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     }
     for (int t = 0; t < T; ++t) {
         const HostTree &ht = *trees[t];
-        for (int i = 0; i < nsub; ++i) {
-            const int g = sub[t][i];
-            parent[g] = i > 0 ? sub[t][i - 1] : -1;
-            bflag[g] = BF_REFINED | BF_SPECIAL;
-            tree[g] = t;
-            child[g * NC] = i + 1 < nsub ? sub[t][i + 1] : gid[t][0];
-            for (int s = 0; s < S; ++s)  // one box per level: its own neighbour across a periodic side
-                if (ht.bct[s] == 2) nb[g * S + s] = g;
-            for (int d = 0; d < NDIR; ++d)  // connected like the root: itself across periodic sides
-                if (ht.boxes[ht.lstart[1]].nb[d] >= 0) nball[(size_t)g * NDIR + d] = g;
-        }
+        const int r1 = ht.lstart[1];
+        for (int i = 0; i < nsub; ++i)
+            for (int r = 0; r < ht.nroots(); ++r) {
+                const int g = sub[t][i] + r;
+                const HBox &root = ht.boxes[r1 + r];
+                parent[g] = i > 0 ? sub[t][i - 1] + r : -1;
+                bflag[g] = BF_REFINED | BF_SPECIAL;
+                tree[g] = t;
+                x0[g] = root.idx[0] - 1;  // unit root boxes
+                child[g * NC] = i + 1 < nsub ? sub[t][i + 1] + r : gid[t][r1 + r];
+                for (int s = 0; s < S; ++s) {  // connected like the roots (a root is its own periodic neighbour)
+                    const int q = root.nb[ht.side_dir(s)];
+                    if (q >= 0) nb[g * S + s] = sub[t][i] + (q - r1);
+                }
+                for (int d = 0; d < NDIR; ++d)
+                    if (root.nb[d] >= 0) nball[(size_t)g * NDIR + d] = sub[t][i] + (root.nb[d] - r1);
+            }
         for (int b = 0; b < (int)ht.boxes.size(); ++b) {
             const HBox &hx = ht.boxes[b];
             const int g = gid[t][b];
             tree[g] = t;
             x0[g] = (hx.idx[0] - 1) * N * hb[g];
             if (hx.level == 1) {
-                parent[g] = nsub > 0 ? sub[t][nsub - 1] : -1;
+                parent[g] = nsub > 0 ? sub[t][nsub - 1] + (b - ht.lstart[1]) : -1;
             } else {
                 parent[g] = gid[t][hx.parent];
                 int p = 0;
@@ -280,6 +287,11 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     }
     meta.nb = upload(nb, own);
     meta.nmask = upload(nmask, own);
+    std::vector<unsigned char> cfmask(nbox, 0);
+    for (int g = 0; g < nbox; ++g)
+        for (int s = 0; s < S; ++s)
+            if (nb[g * S + s] <= -2) cfmask[g] |= (unsigned char)(1u << s);
+    meta.cfmask = upload(cfmask, own);
     meta.parent = upload(parent, own);
     meta.poff = upload(poff, own);
     meta.coff = upload(coff, own);

@@ -128,7 +128,10 @@ class Grid {
     int prolong = 0;
     int *d_nball = nullptr;  // same-level neighbour of every box in all 3^D - 1 directions, -1 none
     // variable coefficients or another prolongation: every level on the per-level kernels
-    bool levels_path() const { return op != 0 || prolong != 0; }
+    bool levels_path() const { return op != 0 || prolong != 0 || roots_levels; }
+    // trees of several root boxes whose coarse grids are device boxes (one per
+    // root and level): the cycle runs on the per-level kernels
+    bool roots_levels = false;
     void correct(Workspace &w, int l, const int *active, cudaStream_t s);
     // no Dirichlet side (single trees): the source is made compatible and the
     // solution kept at zero volume-weighted mean

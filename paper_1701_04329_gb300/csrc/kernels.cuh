@@ -45,6 +45,8 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr unsigned char BF_REFINED = 1, BF_SPECIAL = 2;
 constexpr int BF_NSHIFT = 2;  // flag bits 2..7: Neumann domain sides (bit 2 + s)
+// BoxInfo::flag bits 8..13 (not in the per-box byte): refinement-boundary sides (bit 8 + s)
+constexpr int BF_CF = 0x3f00;
 
 struct BoxMeta {
     const int *nb;
@@ -61,6 +63,7 @@ struct BoxMeta {
     const double *ih2;       // 1/h^2 of every box (an FP64 division costs ~11 FP64-pipe instructions)
     const unsigned char *nmask;  // bit s: side s is a Neumann domain boundary (ghost u + h b, not 2 b - u)
     const double *x0;        // lower x coordinate of every box (the radius in (r,z) coordinates)
+    const unsigned char *cfmask;  // bit s: side s is a refinement boundary (a coarser neighbour)
 };
 
 // Metadata of one box, prefetched into shared memory one box ahead.
@@ -100,10 +103,10 @@ __device__ __forceinline__ void info_load(const BoxMeta &A, int idx, int n, int 
             I.b = b;
             if (b >= 0) {
                 I.coff = A.coff[b];
-                I.flag = A.bflag[b];
+                I.flag = A.bflag[b] | (A.cfmask[b] << 8);
                 I.poff = A.poff[b];
                 I.parent = A.parent[b];
-                I.nmask = I.flag >> BF_NSHIFT;
+                I.nmask = (I.flag >> BF_NSHIFT) & 0x3f;
             }
         }
     }

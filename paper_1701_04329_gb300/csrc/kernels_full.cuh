@@ -118,9 +118,44 @@ __device__ __forceinline__ void fp_issue(const BoxInfo &I, const T *u, const T *
     }
 }
 
-// Completes the ghosts of non-copy faces from the staged u_1 (after the wait).
+// Completes the domain-side ghosts among this thread's own items (the ones
+// fp_issue gave it) from the u_1 it staged there: 2 b - u_1 (Dirichlet) or
+// u_1 + h b (Neumann).  Its own copies are visible to it after its wait, so
+// this needs no barrier.
 template <int D, int M, typename T, int GT>
-__device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const T *u, T *st, int lt, int hom) {
+__device__ __forceinline__ void fp_fix_own(const BoxInfo &I, const BoxMeta &A, T *st, int lt, int hom) {
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC, MH = F::MH;
+    for (int item = lt; item < F::NGI; item += F::G) {
+        if (item < F::NXI) {
+            int s, j, k;
+            fp_xitem<D, M>(item, s, j, k);
+            if (I.code[s] != -1) continue;
+            T &gv = st[2 * F::PT + s * F::ROWS + sp_row<D, M>(j, k)];
+            const T bv = hom ? T(0) : T(A.bc[I.base[s] + k * M + j]);
+            gv = ((I.nmask >> s) & 1) ? fma(T(A.hb[I.b]), bv, gv) : T(2) * bv - gv;
+        } else {
+            int s, col, h0, jg, kg, jin, kin, jm, km;
+            fp_yzitem<D, M, T>(item - F::NXI, s, col, h0, jg, kg, jin, kin, jm, km);
+            if (I.code[s] != -1) continue;
+            T *gv = st + col * F::PT + sp_row<D, M>(jg, kg) * MH + h0;
+            const int rg = (col + jg + kg + D) & 1;
+            const int t2 = (s >> 1) == 1 ? kin : jin;
+            const bool neu = (I.nmask >> s) & 1;
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) {
+                const T bv = hom ? T(0) : T(A.bc[I.base[s] + t2 * M + 2 * (h0 + x) + rg]);
+                gv[x] = neu ? fma(T(A.hb[I.b]), bv, gv[x]) : T(2) * bv - gv[x];
+            }
+        }
+    }
+}
+
+// Completes the ghosts of non-copy faces from the staged u_1 (after the wait;
+// cf_only: the refinement-boundary faces only, fp_fix_own doing the domain sides).
+template <int D, int M, typename T, int GT>
+__device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const T *u, T *st, int lt, int hom,
+                                       bool cf_only = false) {
     using F = FpCfg<D, M, T, GT>;
     constexpr int VEC = F::VEC, MH = F::MH;
     const T c1 = D == 2 ? T(1) : T(1.25);
@@ -130,7 +165,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
             int s, j, k;
             fp_xitem<D, M>(item, s, j, k);
             const int code = I.code[s];
-            if (code >= 0) continue;
+            if (code >= 0 || (cf_only && code == -1)) continue;
             T &gv = st[2 * F::PT + s * F::ROWS + sp_row<D, M>(j, k)];
             const T u1 = gv;
             if (code == -1) {
@@ -149,7 +184,7 @@ __device__ __forceinline__ void fp_fix(const BoxInfo &I, const BoxMeta &A, const
             int s, col, h0, jg, kg, jin, kin, jm, km;
             fp_yzitem<D, M, T>(item - F::NXI, s, col, h0, jg, kg, jin, kin, jm, km);
             const int code = I.code[s];
-            if (code >= 0) continue;
+            if (code >= 0 || (cf_only && code == -1)) continue;
             const int hi = s & 1, a = s >> 1;
             T *gv = st + col * F::PT + sp_row<D, M>(jg, kg) * MH + h0;
             const int rg = (col + jg + kg + D) & 1;  // i-parity of the plane's cells in the ghost row
@@ -221,7 +256,10 @@ __device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, i
 // (or null).  pre(slots) and post(slots) run in every thread of the block
 // before and after the bodies of one step, with the metadata of the step's
 // boxes (one per group).
-template <int D, int M, typename T, int GT, typename Want, typename Flat, typename Body, typename Pre,
+// OWN: the issuing threads complete the domain-side ghosts before the box's
+// barrier (fp_fix_own) and only refinement-boundary boxes take the extra
+// barrier; otherwise every box with a non-copy side takes it (fewer registers).
+template <int D, int M, typename T, int GT, bool OWN = true, typename Want, typename Flat, typename Body, typename Pre,
           typename Post>
 __device__ __forceinline__ void fp_walk(const BoxMeta &A, int b0, int n, const int *list, const T *u, int hom,
                                         Want want, Flat flat, Body body, Pre pre, Post post) {
@@ -249,13 +287,15 @@ __device__ __forceinline__ void fp_walk(const BoxMeta &A, int b0, int n, const i
         cp_wait<NST - 2>();
         const BoxInfo &I = info[(it % NI) * F::BPC + g];
         const bool special = I.b >= 0 && want(I) && (I.flag & BF_SPECIAL);
+        const bool cf = special && (!OWN || (I.flag & BF_CF));
         T *st = stages + ((it % NST) * F::BPC + g) * F::BOX;
-        const int any_special = __syncthreads_or(special);  // previous stage and metadata slot are free now
+        if (OWN && special) fp_fix_own<D, M, T, GT>(I, A, st, lt, hom);  // domain sides: this thread's own items
+        const int any_cf = __syncthreads_or(cf);  // previous stage and metadata slot are free now
         issue(it + NST - 1);
         info_load<D>(A, base + NST * stride + g, n, b0, list, info[((it + NST) % NI) * F::BPC + g], lt, F::G);
         pre(&info[(it % NI) * F::BPC]);
-        if (any_special) {
-            if (special) fp_fix<D, M, T, GT>(I, A, u, st, lt, hom);
+        if (any_cf) {  // refinement-boundary ghosts read cells other threads staged
+            if (cf) fp_fix<D, M, T, GT>(I, A, u, st, lt, hom, OWN);
             __syncthreads();
         }
         if (I.b >= 0) body(I, st, lt);
@@ -445,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_residual_p(BoxMeta A, const i
             cur = tr;
         }
     };
-    fp_walk<D, M, T, GT>(A, 0, n, list, u, hom, want, flat, body, pre, post);
+    fp_walk<D, M, T, GT, false>(A, 0, n, list, u, hom, want, flat, body, pre, post);  // register-bound: no own-thread fix
     flush_max(rm, pm, cur, cur >= 0, rmax, pmax, red);
 }
 
@@ -697,7 +737,9 @@ struct PpCfg {
     static constexpr size_t smem() {
         return sizeof(T) * (2 * IMG * NST + PSZ) + sizeof(BoxInfo) * (NST + 1) + sizeof(long long) * NC * (NST + 1);
     }
-    static constexpr bool ok = F::ok;
+    // a vector stays inside one half-row, and at least two CTAs fit an SM
+    // (3D boxes of 16^3 cells take the per-child kernel)
+    static constexpr bool ok = F::ok && smem() <= 113 * 1024;
 };
 
 // metadata of parent group q: the parent of boxes b0 + NC q .. b0 + NC q + NC - 1
@@ -720,7 +762,7 @@ __device__ __forceinline__ void pp_info_load(const BoxMeta &A, int q, int np, in
         if (on) {
             I.coff = A.coff[b];
             I.flag = A.bflag[b];
-            I.nmask = I.flag >> BF_NSHIFT;
+            I.nmask = (I.flag >> BF_NSHIFT) & 0x3f;
         }
     } else if (lt >= 32 && lt < 32 + S::NC) {
         if (on) ccoff[lt - 32] = A.coff[b0 + S::NC * q + (lt - 32)];

@@ -108,6 +108,7 @@ struct SpPlan {
     using S = SpCfg<D, M, T>;
     static constexpr int NQ = (S::NGI + S::G - 1) / S::G;
     int gdst[NQ], gsrc[NQ];  // dst | side << 16 | scalar << 19 ; nb offset | u1 offset << 16
+    int gbc[NQ];             // boundary data of the item's first face (stride 2 along a y/z item's vector)
     int vdst[S::NIT], vsrc[S::NIT];
     __device__ __forceinline__ void init(int lt, int c) {
         constexpr int MH = S::MH, H = S::H;
@@ -124,15 +125,19 @@ struct SpPlan {
             const int item = lt + q * S::G;
             gdst[q] = -1;
             gsrc[q] = 0;
+            gbc[q] = 0;
             if (item >= S::NGI) continue;
             if (item < 2 * S::NXI) {
                 int sd, j, k;
                 sp_xitem<D, M>(item, c, sd, j, k);
+                gbc[q] = k * M + j;
                 gdst[q] = (S::PT + sd * S::ROWS + sp_row<D, M>(j, k)) | (sd << 16) | (1 << 19);
                 gsrc[q] = ((1 - c) * H + hrow<D, M>(j, k) + (sd ? 0 : MH - 1)) | ((hrow<D, M>(j, k) + (sd ? MH - 1 : 0)) << 16);
             } else {
                 int sd, h0, jg, kg, jin, kin, jm, km;
                 sp_yzitem<D, M, T>(item - 2 * S::NXI, sd, h0, jg, kg, jin, kin, jm, km);
+                const int rg = (c + jin + kin + D) & 1;  // i-parity of the colour-c cells of the inner row
+                gbc[q] = ((sd >> 1) == 1 ? kin : jin) * M + 2 * h0 + rg;
                 gdst[q] = (sp_row<D, M>(jg, kg) * MH + h0) | (sd << 16);
                 gsrc[q] = ((1 - c) * H + hrow<D, M>(jm, km) + h0) | ((hrow<D, M>(jin, kin) + h0) << 16);
             }
@@ -165,10 +170,42 @@ __device__ __forceinline__ void sp_issue(const SpPlan<D, M, T> &pl, const BoxInf
     }
 }
 
-// completes the ghosts of non-copy faces from the staged u_1
+// Completes the domain-side ghosts among this thread's own items from the
+// u_1 it staged there (visible to it after its own wait, before the box's
+// barrier): 2 b - u_1 (Dirichlet) or u_1 + h b (Neumann).
+template <int D, int M, typename T>
+__device__ __forceinline__ void sp_fix_own(const SpPlan<D, M, T> &pl, const BoxInfo &I, const BoxMeta &A, T *box,
+                                           int hom) {
+    using S = SpCfg<D, M, T>;
+    constexpr int VEC = S::VEC;
+#pragma unroll
+    for (int q = 0; q < SpPlan<D, M, T>::NQ; ++q) {
+        const int dst = pl.gdst[q];
+        if (dst < 0) continue;
+        const int sd = (dst >> 16) & 7;
+        if (I.code[sd] != -1) continue;
+        const bool neu = (I.nmask >> sd) & 1;
+        const T hbox = neu ? T(A.hb[I.b]) : T(0);
+        const double *bc = A.bc + I.base[sd] + pl.gbc[q];
+        T *gv = box + (dst & 0xffff);
+        if (dst & (1 << 19)) {
+            const T bv = hom ? T(0) : T(bc[0]);
+            gv[0] = neu ? fma(hbox, bv, gv[0]) : T(2) * bv - gv[0];
+        } else {
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) {
+                const T bv = hom ? T(0) : T(bc[2 * x]);
+                gv[x] = neu ? fma(hbox, bv, gv[x]) : T(2) * bv - gv[x];
+            }
+        }
+    }
+}
+
+// completes the ghosts of non-copy faces from the staged u_1 (cf_only: the
+// refinement-boundary faces only, the domain sides being done by sp_fix_own)
 template <int D, int M, typename T>
 __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const T *u, T *box, int lt, int c,
-                                       int hom) {
+                                       int hom, bool cf_only = false) {
     using S = SpCfg<D, M, T>;
     constexpr int VEC = S::VEC, MH = S::MH;
     T *P = box, *X = box + S::PT;
@@ -180,7 +217,7 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
             int s, j, k;
             sp_xitem<D, M>(item, c, s, j, k);
             const int code = I.code[s];
-            if (code >= 0) continue;
+            if (code >= 0 || (cf_only && code == -1)) continue;
             T &gv = X[s * S::ROWS + sp_row<D, M>(j, k)];
             const T u1 = gv;
             if (code == -1) {
@@ -200,7 +237,7 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
             int s, h0, jg, kg, jin, kin, jm, km;
             sp_yzitem<D, M, T>(item - 2 * S::NXI, s, h0, jg, kg, jin, kin, jm, km);
             const int code = I.code[s];
-            if (code >= 0) continue;
+            if (code >= 0 || (cf_only && code == -1)) continue;
             const int hi = s & 1, a = s >> 1;
             T *gv = P + sp_row<D, M>(jg, kg) * MH + h0;
             const int rg = (c + jin + kin + D) & 1;  // i-parity of the colour-c cells of the inner row
@@ -235,7 +272,7 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
             }
         }
     }
-    if (!I.nmask) return;
+    if (!I.nmask || cf_only) return;
     // Neumann domain sides: g = u_1 + h b (a separate pass keeps the common path lean)
     const T hbox = T(A.hb[I.b]);
     for (int item = lt; item < S::NGI; item += S::G) {
@@ -316,9 +353,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
         const BoxInfo &I = info[(it % NI) * S::BPC + g];
         const int b = I.b;
         const bool special = b >= 0 && (I.flag & BF_SPECIAL);
+        const bool cf = b >= 0 && (I.flag & BF_CF);
         T *box = stages + ((it % NST) * S::BPC + g) * S::BOX;
+        if (special) sp_fix_own<D, M, T>(pl, I, A, box, hom);  // domain sides: this thread's own items
         // one barrier per box: the stage and metadata slot of the previous box are free after it
-        const int any_special = __syncthreads_or(special);
+        const int any_cf = __syncthreads_or(cf);
         {
             const int q = it + NST - 1;
             const BoxInfo &In = info[(q % NI) * S::BPC + g];
@@ -326,8 +365,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
             cp_commit();
         }
         info_load<D>(A, base + NST * stride + g, n, b0, list, info[((it + NST) % NI) * S::BPC + g], lt, S::G);
-        if (any_special) {
-            if (special) sp_fix<D, M, T>(I, A, u, box, lt, c, hom);
+        if (any_cf) {  // refinement-boundary ghosts read cells other threads staged
+            if (cf) sp_fix<D, M, T>(I, A, u, box, lt, c, hom, true);
             __syncthreads();
         }
         if (b >= 0) {

@@ -118,20 +118,6 @@ def test_allocator_needs_both_callbacks():
     assert L.afg_set_allocator(None, None, None) == afgpu.AFG_OK
 
 
-def test_forest_of_a_block_tree_is_refused():
-    """A forest never holds a tree whose level 1 is a block of root boxes,
-    whatever its size; the refusal comes before any device work."""
-    m = afgpu.Tree(2, 8, 3, roots=(2, 1))
-    m.refine_uniform(2)
-    for trees in ([m], [m, afgpu.Tree(2, 8, 3)]):
-        try:
-            afgpu.Forest(trees)
-            assert False, "expected a refusal"
-        except afgpu.AfgError as e:
-            assert e.code == afgpu.AFG_ERR_STATE
-            assert "several root boxes" in str(e)
-
-
 def test_operator_validated_on_the_host():
     """afg_set_operator: known operators only, (r,z) in 2D only, single root
     box; eps needs a variable-coefficient operator first (no GPU needed)."""

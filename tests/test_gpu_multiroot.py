@@ -71,28 +71,65 @@ def test_block_solve_and_mixed_precision(D):
     assert rel_diff(b.get_solution(), a.get_solution()) <= 1e-8
 
 
-def test_forest_of_root_blocks_is_refused():
-    t1 = afgpu.Tree(2, 8, 3, roots=(2, 1))
-    t2 = afgpu.Tree(2, 8, 3)
-    for t in (t1, t2):
-        t.refine_uniform(2)
-    with pytest.raises(afgpu.AfgError):
-        afgpu.Forest([t1, t2])
+def test_block_trees_refuse_what_is_not_built():
+    """The variable-coefficient operators, the other prolongations and
+    singular problems take trees of one root box."""
+    t = afgpu.Tree(2, 8, 3, roots=(2, 1))
+    t.refine_uniform(2)
+    for call in (lambda: t.set_operator(afgpu.AFG_OP_VAR), lambda: t.set_prolongation(afgpu.AFG_PROLONG_ZEROTH)):
+        with pytest.raises(afgpu.AfgError) as e:
+            call()
+        assert e.value.code == afgpu.AFG_ERR_ARG
+    s = afgpu.Tree(2, 8, 3, roots=(2, 1))
+    s.set_boundary_types([2, 2, 1, 1])
+    s.refine_uniform(2)
+    with pytest.raises(afgpu.AfgError) as e:
+        s.set_rhs(torch.zeros(s.n_leaf_cells, dtype=torch.float64, device="cuda"))
+    assert e.value.code == afgpu.AFG_ERR_STATE
+
+
+@pytest.mark.parametrize("D,N,roots,uni,extra,types,seed", [
+    (3, 8, (2, 2, 2), 1, 1, None, 620), (3, 8, (7, 1, 1), 1, 1, [2, 2, 0, 0, 1, 0], 621),
+    (2, 8, (9, 9), 1, 1, None, 622), (3, 16, (2, 1, 1), 1, 1, [0, 0, 1, 0, 0, 0], 623)])
+def test_large_blocks_cycle_by_cycle(D, N, roots, uni, extra, types, seed):
+    """Blocks beyond one CTA's shared memory (a 2 x 2 x 2 or 7 x 1 x 1 block
+    of 8^3 roots, 9 x 9 of 8^2, any block of 16^3): their coarse grids are
+    device boxes, one per root and level, on the per-level kernels."""
+    a, b, rho, bv = block_pair(D, N, roots, uni, extra, seed, types=types, frac=0.3)
+    load(a, b, rho, bv)
+    cycles_parity(a, b, 2)
 
 
 @pytest.mark.parametrize("roots,fits", [((6, 1, 1), True), ((3, 2, 1), True), ((2, 2, 2), False), ((7, 1, 1), False)])
-def test_block_size_limit_of_the_one_cta_bottom(roots, fits):
-    """The documented limit for blocks of 8^3 root boxes (FP64, one CTA's
-    shared memory): 6 x 1 x 1 and 3 x 2 x 1 fit, 2 x 2 x 2 and 7 x 1 x 1 are
-    refused when the device grid is built (the first field call), before
-    any kernel or graph."""
+def test_one_cta_block_bottom_and_per_level_blocks_solve(roots, fits):
+    """Blocks of 8^3 roots on either side of the one-CTA limit solve to the
+    tolerance with the oracle's cycle count."""
+    a = OracleTree(3, 8, 1, roots=roots)
     t = afgpu.Tree(3, 8, 1, roots=roots)
-    rho = torch.ones(t.n_leaf_cells, dtype=torch.float64, device="cuda")
-    if fits:
-        t.set_rhs(rho)
-        st = t.solve(afgpu.default_opts(rel_tol=1e-8, max_cycles=40))
-        assert st["rel_residual"] <= 1e-8
-    else:
-        with pytest.raises(afgpu.AfgError) as e:
-            t.set_rhs(rho)
-        assert e.value.code == afgpu.AFG_ERR_STATE and "too large" in str(e.value)
+    x = a.cell_centers()
+    rho = np.sin(x[:, 0]) + np.cos(2 * x[:, 1]) * x[:, 2]
+    load(a, t, rho, np.zeros(a.n_bfaces))
+    ca = a.solve(1e-8, 60)
+    st = t.solve(afgpu.default_opts(rel_tol=1e-8, max_cycles=60))
+    assert st["cycles"] == ca
+    assert rel_diff(t.get_solution(), a.get_solution()) <= TOL64
+
+
+def test_forest_of_block_trees_matches_per_tree_oracle():
+    """A forest that holds trees of several root boxes (and one of a single
+    root) runs every tree's coarse grids on the per-level kernels."""
+    specs = [((2, 1), 630), ((1, 1), 631), ((1, 3), 632), ((3, 2), 633)]
+    pairs = [block_pair(2, 8, roots, 1, 2, seed) for roots, seed in specs]
+    f = afgpu.Forest([p[1] for p in pairs])
+    f.set_rhs(torch.tensor(np.concatenate([p[2] for p in pairs]), device="cuda"))
+    f.set_dirichlet(torch.tensor(np.concatenate([p[3] for p in pairs]), device="cuda"))
+    st = f.solve(afgpu.default_opts(rel_tol=1e-10, max_cycles=60))
+    u = f.get_solution().cpu().numpy()
+    off = 0
+    for k, (a, _, rho, bv) in enumerate(pairs):
+        a.set_rhs(rho); a.set_dirichlet(bv); a.zero_solution()
+        ca = a.solve(1e-10, 60)
+        n = a.n_leaf_cells
+        assert st[k]["cycles"] == ca, (k, st[k]["cycles"], ca)
+        assert rel_diff(u[off:off + n], a.get_solution()) <= TOL64
+        off += n
