@@ -139,9 +139,10 @@ def kernel_only(args):
 
 
 # DRAM bytes (read + write) per launch of the roofline kernels on the 256^3 level, from one ncu
-# capture of `bench.py --kernel-only smooth [--fp32] --reps 3` of the kernel as it is now; None
-# when that kernel has not been captured since it last changed.
-TRAFFIC = {("k_smooth_p<3,8,double>", 6): 192254464, ("k_smooth_p<3,8,float>", 6): 84442880}
+# capture of `bench.py --kernel-only smooth [--fp32] --reps 3` of the kernel as it is now (the
+# FP32 one homogeneous, as bench.py times it); None when that kernel has not been captured since
+# it last changed.
+TRAFFIC = {("k_smooth_p<3,8,double>", 6): 187878400, ("k_smooth_p<3,8,float>", 6): 80286976}
 TRAFFIC_UNIT = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
 
 
@@ -432,12 +433,13 @@ def bench_forest(K, W_, dev, hbm, dist=None, rank=0, world=1):
     import torch
     from paper_1701_04329_gb300 import afgpu, autotune, shard
     choice = autotune.tuned_choice()
-    box_n, nd, nu = choice or (16, 2, 2)
+    box_n, nd, nu, tpb = choice or (16, 2, 2, 0)
     trees, rhos, bs = shard.build_batch(512, box_n)
     boxes = [t.info().n_boxes for t in trees]
     bins = shard.lpt_partition(boxes, world)
     mine = bins[rank]
-    opts = afgpu.default_opts(rel_tol=1e-8, precision=afgpu.AFG_MIXED, n_down=nd, n_up=nu, max_cycles=60)
+    opts = afgpu.default_opts(rel_tol=1e-8, precision=afgpu.AFG_MIXED, n_down=nd, n_up=nu, max_cycles=60,
+                              threads_per_box=tpb)
     res, f = shard.solve_shard(trees, rhos, bs, mine, opts, dev)
     n_all = int(sum(len(r) for r in rhos))
     for _ in range(W_):
@@ -463,7 +465,8 @@ def bench_forest(K, W_, dev, hbm, dist=None, rank=0, world=1):
     gbs = k32["bytes"] / (k32["ms"] * 1e-3) / 1e9
     out = {"workload": "512 2D quadtrees (seeds 1000+t), 1-4 Gaussian sources, max level 4..9 (8^2 boxes; one "
                        "fewer with 16^2), mixed precision to 1e-8 per tree, CUDA graph",
-           "config": {"box_n": box_n, "n_down": nd, "n_up": nu, "source": "tuned_forest.json" if choice else "default",
+           "config": {"box_n": box_n, "n_down": nd, "n_up": nu, "threads_per_box": tpb,
+                      "source": "tuned_forest.json" if choice else "default",
                       "ranks": world, "split": "whole trees by LPT on box count" if world > 1 else "one forest"},
            "value": n_all / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "unknowns": n_all,
            "gpu_launches_per_step": launches,

@@ -77,6 +77,10 @@ typedef struct {
                           (default 2: each FP64 residual pass, FP64-arithmetic bound, then buys two
                           V-cycles of reduction; 1 gives the plain alternation) */
     int use_graph;     /* 1: replay the cycle as a CUDA graph (default 1) */
+    int threads_per_box; /* FP32 half-sweep (the mixed-precision solves): threads per box, 0 (default) or
+                            one per 16-byte vector of a box's colour half, min(N^D/8, 256), or half as
+                            many (two vectors per thread, twice the boxes per CTA); other values:
+                            AFG_ERR_ARG.  The FP64 kernels take one thread per vector. */
 } afg_mg_opts;
 
 typedef struct {
@@ -333,21 +337,23 @@ int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree
  * runs fix the box size and N_down = N_up = 2).  candidates[n]: forests of
  * the same problems built with different box sizes (8^2 and 16^2 cells, the
  * finest spacing equal), each with its source term and boundary data set.
- * json_in (may be NULL): {"sweeps": [[n_down, n_up], ...], "reps": R},
- * default sweeps [[1,1],[2,2],[3,3]] and R = 3.  For every candidate and
- * pair it runs afg_forest_solve with `base` (NULL: mixed precision to 1e-8)
- * and that pair -- one warm-up solve, which also captures the CUDA graphs,
- * then the fastest of R solves timed with CUDA events on the forest's
- * stream -- and writes to json_out (cap bytes, NUL-terminated) the report
- * {"objective": "unknowns_per_s", "best": ROW, "table": [ROW, ...]}, ROW =
- * {"candidate", "box_n", "n_down", "n_up", "ms", "unknowns",
- * "unknowns_per_s", "converged", "worst_rel_residual", "max_cycles"}.  The
- * best row is the converged one with the most unknowns per second: time to
- * the tolerance per unknown, which compares the box sizes' different meshes
- * per unknown.  Threads per box are not a knob: every kernel gives one
- * thread to each 16-byte vector of a box's colour half, which the box size
- * fixes.  AFG_ERR_ARG on a malformed json_in or a too small json_out (the
- * message gives the size needed).  Each forest's solution is overwritten. */
+ * json_in (may be NULL): {"sweeps": [[n_down, n_up], ...],
+ * "vectors_per_thread": [1, 2], "reps": R}, default sweeps [[1,1],[2,2],
+ * [3,3]], vectors per thread [1] (1: the FP32 half-sweep's one thread per
+ * 16-byte vector of a box's colour half, 2: half as many threads per box;
+ * afg_mg_opts.threads_per_box) and R = 3.  For every candidate, pair and
+ * threads-per-box choice it runs afg_forest_solve with `base` (NULL: mixed
+ * precision to 1e-8) -- one warm-up solve, which also captures the CUDA
+ * graphs, then the fastest of R solves timed with CUDA events on the
+ * forest's stream -- and writes to json_out (cap bytes, NUL-terminated) the
+ * report {"objective": "unknowns_per_s", "best": ROW, "table": [ROW, ...]},
+ * ROW = {"candidate", "box_n", "n_down", "n_up", "threads_per_box", "ms",
+ * "unknowns", "unknowns_per_s", "converged", "worst_rel_residual",
+ * "max_cycles"}.  The best row is the converged one with the most unknowns
+ * per second: time to the tolerance per unknown, which compares the box
+ * sizes' different meshes per unknown.  AFG_ERR_ARG on a malformed json_in
+ * or a too small json_out (the message gives the size needed).  Each
+ * forest's solution is overwritten. */
 int afg_autotune(afg_forest *const *candidates, int n, const afg_mg_opts *base, const char *json_in,
                  char *json_out, size_t cap);
 

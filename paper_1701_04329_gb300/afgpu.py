@@ -31,7 +31,7 @@ class AfgError(RuntimeError):
 class MgOpts(ctypes.Structure):
     _fields_ = [("n_down", ctypes.c_int), ("n_up", ctypes.c_int), ("n_base", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("rel_tol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("inner_vcycles", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("inner_vcycles", ctypes.c_int), ("use_graph", ctypes.c_int), ("threads_per_box", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -4,11 +4,11 @@ For a workload of independent 2D quadtrees it builds the forest with boxes
 of 8^2 and of 16^2 cells (one level fewer with 16^2, so the finest spacing
 is the same) and hands both to the library's tuner (``afg_autotune``), which
 times the solve to the tolerance for every pair of smoothing steps (N_down,
-N_up) and picks the configuration with the most unknowns per second (time
-to the tolerance per unknown: the two box sizes refine to different meshes
-at the same finest spacing).  Threads per box are not a free knob: every
-kernel gives one thread to each 16-byte vector of a box's colour half, so
-the box size fixes them; the tuner reports them.
+N_up) and every threads-per-box choice of the FP32 half-sweep (one thread
+per 16-byte vector of a box's colour half, or half as many) and picks the
+configuration with the most unknowns per second (time to the tolerance per
+unknown: the two box sizes refine to different meshes at the same finest
+spacing).
 
 ``python -m paper_1701_04329_gb300.autotune 512`` on a GPU writes the choice
 to ``tuned_forest.json`` beside this file; ``bench.py`` times the batched
@@ -41,16 +41,9 @@ def build_forest(n_trees, box_n, seed0=1000, max_level_cap=None):
     return trees, np.concatenate(rhos), np.concatenate(bs)
 
 
-def threads_per_box(dim, box_n, fp32=True):
-    half = box_n ** dim // 2
-    vec = 4 if fp32 else 2
-    return min(max(half // vec, 1), 256)
-
-
 def autotune_forest(n_trees=512, seed0=1000, tol=1e-8, precision=afgpu.AFG_MIXED, box_sizes=(8, 16),
-                    sweeps=((1, 1), (2, 2), (3, 3)), reps=3, max_level_cap=None):
-    """Returns (best, table) from afg_autotune, rows extended with the
-    threads per box."""
+                    sweeps=((1, 1), (2, 2), (3, 3)), vectors_per_thread=(1, 2), reps=3, max_level_cap=None):
+    """Returns (best, table) from afg_autotune."""
     import torch
     forests, keep = [], []
     for box_n in box_sizes:
@@ -61,15 +54,14 @@ def autotune_forest(n_trees=512, seed0=1000, tol=1e-8, precision=afgpu.AFG_MIXED
         forests.append(f)
         keep.append(trees)
     base = afgpu.default_opts(rel_tol=tol, precision=precision, max_cycles=60)
-    spec = json.dumps({"sweeps": [list(s) for s in sweeps], "reps": reps}).encode()
+    spec = json.dumps({"sweeps": [list(s) for s in sweeps], "vectors_per_thread": list(vectors_per_thread),
+                       "reps": reps}).encode()
     out = ctypes.create_string_buffer(1 << 16)
     arr = (ctypes.c_void_p * len(forests))(*[f._h.value for f in forests])
     for f in forests:
         f._sync_stream()
     afgpu._check(afgpu.lib().afg_autotune(arr, len(forests), ctypes.byref(base), spec, out, len(out)))
     rep = json.loads(out.value.decode())
-    for r in rep["table"] + [rep["best"]]:
-        r["threads_per_box"] = threads_per_box(2, r["box_n"])
     for f in forests:
         f.close()
     for trees in keep:
@@ -86,11 +78,11 @@ def record(best, table, n_trees, tol, path=TUNED):
 
 
 def tuned_choice(path=TUNED):
-    """The recorded choice (box_n, n_down, n_up), or None."""
+    """The recorded choice (box_n, n_down, n_up, threads_per_box), or None."""
     try:
         with open(path) as f:
             b = json.load(f)["best"]
-        return int(b["box_n"]), int(b["n_down"]), int(b["n_up"])
+        return int(b["box_n"]), int(b["n_down"]), int(b["n_up"]), int(b.get("threads_per_box", 0))
     except (OSError, KeyError, ValueError):
         return None
 

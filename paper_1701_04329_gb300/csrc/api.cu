@@ -49,6 +49,7 @@ cudaStream_t capture_stream() {
 
 template <typename F>
 void run(Grid &g, std::tuple<int, int, int, int, int> key, bool use_graph, cudaStream_t s, F &&body) {
+    std::get<0>(key) += 1000 * g.vpt;  // a graph per threads-per-box choice
     if (!use_graph) {
         body(s);
         return;
@@ -95,12 +96,25 @@ afg_mg_opts opts_or_default(const afg_mg_opts *o) {
     return o ? *o : d;
 }
 
+// threads per box of the FP32 half-sweep: 0 or one per 16-byte vector of a
+// box's colour half (vpt 1), or half as many (vpt 2)
+int vpt_of(const Grid &g, const afg_mg_opts &o, int *vpt) {
+    const int half = (g.D == 2 ? g.N * g.N : g.N * g.N * g.N) / 2;
+    const int nv = std::min(half / 4, 256);
+    if (o.threads_per_box == 0 || o.threads_per_box == nv) *vpt = 1;
+    else if (o.threads_per_box == nv / 2 && nv >= 2) *vpt = 2;
+    else return fail(AFG_ERR_ARG, "threads_per_box must be 0, " + std::to_string(nv) + " or " +
+                                      std::to_string(nv / 2) + " for these boxes");
+    return AFG_OK;
+}
+
 int validate(const afg_mg_opts &o) {
     if (o.n_down < 0 || o.n_up < 0 || o.n_base < 1 || o.n_down > 64 || o.n_up > 64 || o.n_base > 1024)
         return fail(AFG_ERR_ARG, "smoothing steps out of range");
     if (o.max_cycles < 1 || !(o.rel_tol >= 0.0)) return fail(AFG_ERR_ARG, "bad max_cycles / rel_tol");
     if (o.precision != AFG_FP64 && o.precision != AFG_MIXED) return fail(AFG_ERR_ARG, "bad precision");
     if (o.inner_vcycles < 1 || o.inner_vcycles > 16) return fail(AFG_ERR_ARG, "inner_vcycles out of range");
+    if (o.threads_per_box < 0) return fail(AFG_ERR_ARG, "threads_per_box out of range");
     return AFG_OK;
 }
 
@@ -363,6 +377,7 @@ void afg_default_opts(afg_mg_opts *o) {
     o->precision = AFG_FP64;
     o->inner_vcycles = 2;
     o->use_graph = 1;
+    o->threads_per_box = 0;
 }
 
 const char *afg_last_error(void) { return g_err.c_str(); }
@@ -731,6 +746,7 @@ static int one_cycle(afg_tree *t, const afg_mg_opts *opts, afg_stats *st, bool f
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     if (int rc = ready(g)) return rc;
+    if (int rc = vpt_of(g, o, &g.vpt)) return rc;
     const auto t0 = clk::now();
     const afg::MgOpts mo{o.n_down, o.n_up, o.n_base};
     g.make_compatible(t->stream);
@@ -761,6 +777,7 @@ int afg_solve(afg_tree *t, const afg_mg_opts *opts, afg_stats *st) {
     AFG_ON_DEVICE(t);
     Grid &g = grid_of(t);
     if (int rc = ready(g)) return rc;
+    if (int rc = vpt_of(g, o, &g.vpt)) return rc;
     const auto t0 = clk::now();
     std::vector<std::vector<double>> hist;
     const int cycles = o.precision == AFG_MIXED ? solve_mixed(g, o, t->stream, hist)
@@ -909,6 +926,7 @@ int afg_forest_solve(afg_forest *f, const afg_mg_opts *opts, afg_stats *per_tree
     AFG_ON_FOREST_DEVICE(f);
     Grid &g = *f->grid;
     if (int rc = ready(g)) return rc;
+    if (int rc = vpt_of(g, o, &g.vpt)) return rc;
     const auto t0 = clk::now();
     check(cudaMemsetAsync(g.ws64.u->p, 0, (size_t)g.ncell * 8, f->stream), "zero");
     std::vector<std::vector<double>> hist;

@@ -50,7 +50,7 @@ bool json_ints(const char *js, const char *key, std::vector<int> &out, std::stri
 }
 
 struct Row {
-    int cand, box_n, nd, nu, max_cycles;
+    int cand, box_n, nd, nu, tpb, max_cycles;
     double ms, unknowns, worst;
     bool converged;
 };
@@ -62,10 +62,14 @@ extern "C" int afg_autotune(afg_forest *const *cands, int n, const afg_mg_opts *
     if (!cands || n < 1 || !json_out || cap < 2) return afg::api_fail(AFG_ERR_ARG, "bad arguments");
     for (int i = 0; i < n; ++i)
         if (!cands[i] || !cands[i]->grid) return afg::api_fail(AFG_ERR_ARG, "null candidate forest");
-    std::vector<int> sw, reps_v;
+    std::vector<int> sw, reps_v, vpts;
     std::string err;
-    if (!json_ints(json_in, "sweeps", sw, err) || !json_ints(json_in, "reps", reps_v, err))
+    if (!json_ints(json_in, "sweeps", sw, err) || !json_ints(json_in, "reps", reps_v, err) ||
+        !json_ints(json_in, "vectors_per_thread", vpts, err))
         return afg::api_fail(AFG_ERR_ARG, "json_in: " + err);
+    if (vpts.empty()) vpts = {1};
+    for (int v : vpts)
+        if (v != 1 && v != 2) return afg::api_fail(AFG_ERR_ARG, "json_in: vectors_per_thread must be 1 or 2");
     if (sw.empty()) sw = {1, 1, 2, 2, 3, 3};
     if (sw.size() % 2) return afg::api_fail(AFG_ERR_ARG, "json_in: sweeps must be pairs [n_down, n_up]");
     const int reps = reps_v.empty() ? 3 : reps_v[0];
@@ -89,10 +93,15 @@ extern "C" int afg_autotune(afg_forest *const *cands, int n, const afg_mg_opts *
             cudaEvent_t e0, e1;
             afg::check(cudaEventCreate(&e0), "event");
             afg::check(cudaEventCreate(&e1), "event");
-            for (size_t k = 0; k + 1 < sw.size(); k += 2) {
+            const int half = (g.D == 2 ? g.N * g.N : g.N * g.N * g.N) / 2;
+            const int nv = std::min(half / 4, 256);
+            for (size_t k = 0; k + 1 < sw.size(); k += 2)
+            for (int vp : vpts) {
+                if (nv / vp < 1) continue;
                 afg_mg_opts o = o0;
                 o.n_down = sw[k];
                 o.n_up = sw[k + 1];
+                o.threads_per_box = nv / vp;
                 int rc = afg_forest_solve(f, &o, st.data());  // warm-up: captures the graphs
                 if (rc != AFG_OK && rc != AFG_ERR_NOT_CONVERGED) return rc;
                 float best = 1e30f;
@@ -106,7 +115,7 @@ extern "C" int afg_autotune(afg_forest *const *cands, int n, const afg_mg_opts *
                     afg::check(cudaEventElapsedTime(&ms, e0, e1), "event");
                     best = std::min(best, ms);
                 }
-                Row row{c, g.N, o.n_down, o.n_up, 0, best, unknowns, 0.0, true};
+                Row row{c, g.N, o.n_down, o.n_up, o.threads_per_box, 0, best, unknowns, 0.0, true};
                 for (int t = 0; t < g.T; ++t) {
                     row.worst = std::max(row.worst, st[t].rel_residual);
                     row.max_cycles = std::max(row.max_cycles, st[t].cycles);
@@ -133,10 +142,10 @@ extern "C" int afg_autotune(afg_forest *const *cands, int n, const afg_mg_opts *
     auto row_json = [](const Row &r) {
         char b[512];
         std::snprintf(b, sizeof b,
-                      "{\"candidate\": %d, \"box_n\": %d, \"n_down\": %d, \"n_up\": %d, \"ms\": %.6g, "
-                      "\"unknowns\": %.0f, \"unknowns_per_s\": %.6g, \"converged\": %s, "
+                      "{\"candidate\": %d, \"box_n\": %d, \"n_down\": %d, \"n_up\": %d, \"threads_per_box\": %d, "
+                      "\"ms\": %.6g, \"unknowns\": %.0f, \"unknowns_per_s\": %.6g, \"converged\": %s, "
                       "\"worst_rel_residual\": %.6g, \"max_cycles\": %d}",
-                      r.cand, r.box_n, r.nd, r.nu, r.ms, r.unknowns, r.unknowns / (r.ms * 1e-3),
+                      r.cand, r.box_n, r.nd, r.nu, r.tpb, r.ms, r.unknowns, r.unknowns / (r.ms * 1e-3),
                       r.converged ? "true" : "false", r.worst, r.max_cycles);
         return std::string(b);
     };

@@ -402,7 +402,8 @@ void Grid::smooth(Workspace &w, int l, int steps, int hom, const int *active, cu
     Level &v = L(l);
     BoxMeta A = meta;
     A.active = active;
-    const LaunchCfg c = cfg(l, w.fp64, s);
+    LaunchCfg c = cfg(l, w.fp64, s);
+    c.vpt = vpt;
     for (int it = 0; it < steps; ++it)
         for (int col = 0; col < 2; ++col) {
             if (op) launch_var_smooth(c, A, v.b0, v.nb, w.u->p, w.rho->p, eps_of(w), col, hom, op);

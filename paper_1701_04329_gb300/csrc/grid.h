@@ -129,6 +129,7 @@ class Grid {
     int *d_nball = nullptr;  // same-level neighbour of every box in all 3^D - 1 directions, -1 none
     // variable coefficients or another prolongation: every level on the per-level kernels
     bool levels_path() const { return op != 0 || prolong != 0 || roots_levels; }
+    int vpt = 1;  // FP32 half-sweep: 16-byte vectors per thread (the threads-per-box option)
     // trees of several root boxes whose coarse grids are device boxes (one per
     // root and level): the cycle runs on the per-level kernels
     bool roots_levels = false;

@@ -49,7 +49,9 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int D, int M, typename T>
+// VPT: 16-byte vectors of a box's colour half per thread (1: one thread per
+// vector; 2: half as many threads per box, twice the boxes per CTA)
+template <int D, int M, typename T, int VPT = 1>
 struct SpCfg {
     static constexpr int VEC = 16 / (int)sizeof(T);
     static constexpr int MH = M / 2;
@@ -61,7 +63,7 @@ struct SpCfg {
     static constexpr int NVR = MH / VEC;
     static constexpr int FR = D == 2 ? 1 : M;
     static constexpr int NV = H / VEC;
-    static constexpr int G = NV < kThreads ? NV : kThreads;
+    static constexpr int G = (NV / VPT > 0 ? NV / VPT : 1) < kThreads ? (NV / VPT > 0 ? NV / VPT : 1) : kThreads;
     static constexpr int BPC = kThreads / G;
     static constexpr int NIT = (NV + G - 1) / G;
     static constexpr int NXI = (D == 2 ? M : M * M) / 2;
@@ -103,9 +105,9 @@ __device__ __forceinline__ void sp_yzitem(int it2, int &s, int &h0, int &jg, int
 // for each ghost item of the thread, the destination in the box's stage, the
 // side, whether it is a scalar (x side), and the source offsets relative to
 // the neighbour box (same-level copy) and to the box's own colour-c half (u_1).
-template <int D, int M, typename T>
+template <int D, int M, typename T, int VPT = 1>
 struct SpPlan {
-    using S = SpCfg<D, M, T>;
+    using S = SpCfg<D, M, T, VPT>;
     static constexpr int NQ = (S::NGI + S::G - 1) / S::G;
     int gdst[NQ], gsrc[NQ];  // dst | side << 16 | scalar << 19 ; nb offset | u1 offset << 16
     int gbc[NQ];             // boundary data of the item's first face (stride 2 along a y/z item's vector)
@@ -145,10 +147,10 @@ struct SpPlan {
     }
 };
 
-template <int D, int M, typename T>
-__device__ __forceinline__ void sp_issue(const SpPlan<D, M, T> &pl, const BoxInfo &I, const T *u, const T *rho,
+template <int D, int M, typename T, int VPT>
+__device__ __forceinline__ void sp_issue(const SpPlan<D, M, T, VPT> &pl, const BoxInfo &I, const T *u, const T *rho,
                                          T *box, int lt, int c) {
-    using S = SpCfg<D, M, T>;
+    using S = SpCfg<D, M, T, VPT>;
     constexpr int VEC = S::VEC, H = S::H;
     const T *uo = u + I.coff + (1 - c) * H, *uc = u + I.coff + c * H;
     T *R = box + S::PT + S::XT;
@@ -160,7 +162,7 @@ __device__ __forceinline__ void sp_issue(const SpPlan<D, M, T> &pl, const BoxInf
         cp_async<16>(R + v * VEC, rho + I.coff + c * H + v * VEC);
     }
 #pragma unroll
-    for (int q = 0; q < SpPlan<D, M, T>::NQ; ++q) {
+    for (int q = 0; q < SpPlan<D, M, T, VPT>::NQ; ++q) {
         const int dst = pl.gdst[q];
         if (dst < 0) continue;
         const int sd = (dst >> 16) & 7;
@@ -173,13 +175,13 @@ __device__ __forceinline__ void sp_issue(const SpPlan<D, M, T> &pl, const BoxInf
 // Completes the domain-side ghosts among this thread's own items from the
 // u_1 it staged there (visible to it after its own wait, before the box's
 // barrier): 2 b - u_1 (Dirichlet) or u_1 + h b (Neumann).
-template <int D, int M, typename T>
-__device__ __forceinline__ void sp_fix_own(const SpPlan<D, M, T> &pl, const BoxInfo &I, const BoxMeta &A, T *box,
+template <int D, int M, typename T, int VPT>
+__device__ __forceinline__ void sp_fix_own(const SpPlan<D, M, T, VPT> &pl, const BoxInfo &I, const BoxMeta &A, T *box,
                                            int hom) {
-    using S = SpCfg<D, M, T>;
+    using S = SpCfg<D, M, T, VPT>;
     constexpr int VEC = S::VEC;
 #pragma unroll
-    for (int q = 0; q < SpPlan<D, M, T>::NQ; ++q) {
+    for (int q = 0; q < SpPlan<D, M, T, VPT>::NQ; ++q) {
         const int dst = pl.gdst[q];
         if (dst < 0) continue;
         const int sd = (dst >> 16) & 7;
@@ -203,10 +205,10 @@ __device__ __forceinline__ void sp_fix_own(const SpPlan<D, M, T> &pl, const BoxI
 
 // completes the ghosts of non-copy faces from the staged u_1 (cf_only: the
 // refinement-boundary faces only, the domain sides being done by sp_fix_own)
-template <int D, int M, typename T>
+template <int D, int M, typename T, int VPT = 1>
 __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const T *u, T *box, int lt, int c,
                                        int hom, bool cf_only = false) {
-    using S = SpCfg<D, M, T>;
+    using S = SpCfg<D, M, T, VPT>;
     constexpr int VEC = S::VEC, MH = S::MH;
     T *P = box, *X = box + S::PT;
     const T c1 = D == 2 ? T(1) : T(1.25);
@@ -304,11 +306,11 @@ __device__ __forceinline__ void sp_fix(const BoxInfo &I, const BoxMeta &A, const
 constexpr int kSmoothMinBlocks32 = 6, kSmoothMinBlocks64 = 5;
 
 // scaled = 1: rho holds -h^2 rho / (2D) and the update is u = sum/(2D) + rho
-template <int D, int M, typename T>
+template <int D, int M, typename T, int VPT = 1>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 : kSmoothMinBlocks64) k_smooth_p(BoxMeta A, int b0, int n, const int *list, T *u,
                                                        const T *__restrict__ rho, T h2, int colour, int hom,
                                                        int scaled) {
-    using S = SpCfg<D, M, T>;
+    using S = SpCfg<D, M, T, VPT>;
     constexpr int VEC = S::VEC, MH = S::MH, H = S::H, NST = S::NST, NI = NST + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = threadIdx.x / S::G, lt = threadIdx.x % S::G;
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
     const T inv = T(1) / T(2 * D);
     const int stride = gridDim.x * S::BPC;
     const int first = blockIdx.x * S::BPC;
-    SpPlan<D, M, T> pl;
+    SpPlan<D, M, T, VPT> pl;
     pl.init(lt, c);
     // per vector of this thread, the same for every box: the stage offset of
     // the x neighbour past the vector (half-row or x ghost) and the parity of
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
     __syncthreads();
     for (int q = 0; q < NST - 1; ++q) {
         const BoxInfo &In = info[q * S::BPC + g];
-        if (In.b >= 0) sp_issue<D, M, T>(pl, In, u, rho, stages + (q * S::BPC + g) * S::BOX, lt, c);
+        if (In.b >= 0) sp_issue<D, M, T, VPT>(pl, In, u, rho, stages + (q * S::BPC + g) * S::BOX, lt, c);
         cp_commit();
     }
     int it = 0;
@@ -355,18 +357,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kSmoothMinBlocks32 
         const bool special = b >= 0 && (I.flag & BF_SPECIAL);
         const bool cf = b >= 0 && (I.flag & BF_CF);
         T *box = stages + ((it % NST) * S::BPC + g) * S::BOX;
-        if (special) sp_fix_own<D, M, T>(pl, I, A, box, hom);  // domain sides: this thread's own items
+        if (special) sp_fix_own<D, M, T, VPT>(pl, I, A, box, hom);  // domain sides: this thread's own items
         // one barrier per box: the stage and metadata slot of the previous box are free after it
         const int any_cf = __syncthreads_or(cf);
         {
             const int q = it + NST - 1;
             const BoxInfo &In = info[(q % NI) * S::BPC + g];
-            if (In.b >= 0) sp_issue<D, M, T>(pl, In, u, rho, stages + ((q % NST) * S::BPC + g) * S::BOX, lt, c);
+            if (In.b >= 0) sp_issue<D, M, T, VPT>(pl, In, u, rho, stages + ((q % NST) * S::BPC + g) * S::BOX, lt, c);
             cp_commit();
         }
         info_load<D>(A, base + NST * stride + g, n, b0, list, info[((it + NST) % NI) * S::BPC + g], lt, S::G);
         if (any_cf) {  // refinement-boundary ghosts read cells other threads staged
-            if (cf) sp_fix<D, M, T>(I, A, u, box, lt, c, hom, true);
+            if (cf) sp_fix<D, M, T, VPT>(I, A, u, box, lt, c, hom, true);
             __syncthreads();
         }
         if (b >= 0) {

@@ -17,6 +17,9 @@ struct LaunchCfg {
     // the boxes of the range come in sibling groups: 2^D consecutive boxes
     // share a parent, child c of a group at offset bit a = (c >> a) & 1
     bool sibs = false;
+    // FP32 half-sweep: 16-byte vectors per thread (1: one thread per vector of
+    // a box's colour half; 2: half the threads per box)
+    int vpt = 1;
 };
 
 // counts launches of this library's kernels (host side)

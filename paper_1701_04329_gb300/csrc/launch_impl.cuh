@@ -58,6 +58,18 @@ void do_smooth(const LaunchCfg &c, const BoxMeta &A, int b0, int n, const int *l
     // FP32: the staged half-row kernel; FP64 keeps the table-driven one unless
     // kStagedSmooth64 is set
     if constexpr (SpCfg<D, M, T>::ok && (sizeof(T) == 4 || kStagedSmooth64)) {
+        // FP32 with half the threads per box (two vectors per thread) on request
+        if constexpr (sizeof(T) == 4 && SpCfg<D, M, T>::NV >= 2) {
+            if (c.vpt == 2) {
+                using S = SpCfg<D, M, T, 2>;
+                const size_t smem = S::smem();
+                auto k = k_smooth_p<D, M, T, 2>;
+                launch_pdl(k, grid_for(k, smem, (n + S::BPC - 1) / S::BPC), smem, c.stream, A, b0, n, list, (T *)u,
+                           (const T *)(rhoh ? rhoh : rho), T(h2), colour, hom, rhoh ? 1 : 0);
+                ++g_launches;
+                return;
+            }
+        }
         {
             using S = SpCfg<D, M, T>;
             const size_t smem = S::smem();

@@ -1,7 +1,8 @@
 """The forest autotuner (afg_autotune, called from Python): every candidate
 converges, the choice is the converged candidate with the most unknowns per
-second, box sizes 8 and 16 give the same finest spacing, and a malformed
-search space is refused."""
+second, box sizes 8 and 16 give the same finest spacing, both threads-per-box
+choices of the FP32 half-sweep are tried, and a malformed search space is
+refused."""
 import ctypes
 
 import pytest
@@ -14,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 def test_autotuner_picks_most_unknowns_per_second():
     best, table = autotune.autotune_forest(n_trees=8, reps=1, max_level_cap=6, sweeps=((1, 1), (2, 2)))
-    assert len(table) == 4
+    assert len(table) == 8  # 2 box sizes x 2 sweep pairs x 2 threads-per-box choices
+    assert {r["threads_per_box"] for r in table} == {4, 8, 16, 32}  # 8^2 boxes: 8 or 4; 16^2: 32 or 16
     assert all(r["converged"] for r in table)
     assert best["unknowns_per_s"] == max(r["unknowns_per_s"] for r in table)
     for r in table:
@@ -31,7 +33,7 @@ def test_autotune_rejects_a_malformed_search_space():
     f.set_rhs(torch.tensor(rho, device="cuda"))
     arr = (ctypes.c_void_p * 1)(f._h.value)
     out = ctypes.create_string_buffer(4096)
-    for bad in (b'{"sweeps": [[1, 1], [2]]}', b'{"reps": 0}', b'{"sweeps": [[1, x]]}'):
+    for bad in (b'{"sweeps": [[1, 1], [2]]}', b'{"reps": 0}', b'{"sweeps": [[1, x]]}', b'{"vectors_per_thread": [3]}'):
         rc = afgpu.lib().afg_autotune(arr, 1, None, bad, out, len(out))
         assert rc == afgpu.AFG_ERR_ARG, bad
     small = ctypes.create_string_buffer(16)

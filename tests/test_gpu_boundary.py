@@ -69,3 +69,25 @@ def test_cell_centres_on_the_device_equal_the_host_ones(D, roots):
     host = t.cell_centers()
     dev = t.cell_centers_device().cpu().numpy()
     assert np.array_equal(host, dev)
+
+
+@pytest.mark.parametrize("D,N", [(2, 8), (2, 16), (3, 8)])
+def test_threads_per_box_choices_give_the_same_mixed_solve(D, N):
+    """The FP32 half-sweep with half the threads per box (two vectors per
+    thread) computes the same cells from the same staged data: the mixed
+    solve is bit for bit the same; other values are refused."""
+    from tests.gpu_helpers import pair_random
+    _, b, rho, bv = pair_random(D, N, 2, 1, 40 + N)
+    b.set_rhs(torch.tensor(rho, device="cuda"))
+    b.set_dirichlet(torch.tensor(bv, device="cuda"))
+    nv = min((N ** D // 2) // 4, 256)
+    sols = []
+    for tpb in (0, nv, nv // 2):
+        b.set_solution(torch.zeros(len(rho), dtype=torch.float64, device="cuda"))
+        st = b.solve(afgpu.default_opts(rel_tol=1e-10, precision=afgpu.AFG_MIXED, threads_per_box=tpb))
+        sols.append((st["cycles"], b.get_solution().clone()))
+    assert sols[0][0] == sols[1][0] == sols[2][0]
+    assert torch.equal(sols[0][1], sols[1][1]) and torch.equal(sols[0][1], sols[2][1])
+    with pytest.raises(afgpu.AfgError) as e:
+        b.solve(afgpu.default_opts(rel_tol=1e-10, precision=afgpu.AFG_MIXED, threads_per_box=nv + 1))
+    assert e.value.code == afgpu.AFG_ERR_ARG

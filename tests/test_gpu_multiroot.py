@@ -1,7 +1,9 @@
-"""Trees whose level 1 is a block of root boxes on the GPU (the block bottom
-solve, CUDA kernels through the C ABI) against the FP64 CPU oracle on the
-same seeded inputs: cycle-by-cycle FP64 parity (1e-12 relative after the
-same cycles), solves and mixed precision.  Sec. 2.2 of arXiv:1701.04329
+"""Trees whose level 1 is a block of root boxes on the GPU (the one-CTA block
+bottom solve, or -- beyond one CTA's shared memory and in forests -- their
+coarse grids as device boxes on the per-level kernels; CUDA kernels through
+the C ABI) against the FP64 CPU oracle on the same seeded inputs:
+cycle-by-cycle FP64 parity (1e-12 relative after the same cycles), solves
+and mixed precision.  Sec. 2.2 of arXiv:1701.04329
 (several root boxes) and Sec. 3.2 (several boxes on the coarse grids)."""
 import numpy as np
 import pytest
