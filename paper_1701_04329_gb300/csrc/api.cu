@@ -61,9 +61,10 @@ void run(Grid &g, std::tuple<int, int, int, int, int> key, bool use_graph, cudaS
         try {
             body(cs);
         } catch (...) {
-            cudaGraph_t gr;
+            cudaGraph_t gr = nullptr;
             cudaStreamEndCapture(cs, &gr);
             if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();  // the invalidated capture's status must not reach the next call
             throw;
         }
         cudaGraph_t gr;

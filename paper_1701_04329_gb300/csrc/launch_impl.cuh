@@ -178,7 +178,7 @@ void do_leaf_residual(const LaunchCfg &c, const BoxMeta &A, const int *list, int
                    pmax, out);
     };
     if constexpr (FpCfg<D, M, T>::ok) {
-        using F = FpCfg<D, M, T, fas_threads<D, M, T>()>;
+        using F = FpCfg<D, M, T, leaf_threads<D, M, T>()>;
         const int wc = (n + F::BPC - 1) / F::BPC;
         if (rout_f32) go(k_leaf_residual_p<D, M, T, float>, F::smem(), wc, (float *)rout);
         else go(k_leaf_residual_p<D, M, T, double>, F::smem(), wc, (double *)rout);
