@@ -116,6 +116,13 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
         tree_cells.push_back(trees[t]->n_leaf_cells);
         tree_faces.push_back(trees[t]->n_bfaces);
     }
+    // one tree of one root box: level 2 (the root's 2^D children, one grid of
+    // 2N cells per side) joins the bottom launch where it fits shared memory
+    if (T == 1 && !multi && lmax >= 2) {
+        const long long cells2 = D == 2 ? 4LL * N * N : 8LL * N * N * N;
+        btop32 = bottom_smem(D, false, 2 * N) <= max_smem_optin() ? 2 : 1;
+        btop64 = cells2 <= 1024 && bottom_smem(D, true, 2 * N) <= max_smem_optin() ? 2 : 1;
+    }
     // global box ids: level-major, then tree, then the tree's canonical order
     std::vector<std::vector<int>> gid(T), sub(T, std::vector<int>(nsub, -1));
     for (int t = 0; t < T; ++t) gid[t].assign(trees[t]->boxes.size(), -1);
@@ -436,25 +443,28 @@ void Grid::bottom(Workspace &w, int ltop, int mode, const MgOpts &o, int hom, co
                             w.vold->p, o.n_down, o.n_up, o.n_base, hom);
         return;
     }
-    int b0[4] = {0, 0, 0, 0};
-    for (int l = lmin; l <= 1; ++l) b0[l - lmin] = L(l).b0;
-    launch_bottom(cfg(1, w.fp64, s), A, T, N, lmin, ltop, mode, w.u->p, w.rho->p, w.vold->p, o.n_down, o.n_up,
+    const int top = btop(w);
+    int b0[kBottomLevels] = {};
+    for (int l = lmin; l <= top; ++l) b0[l - lmin] = L(l).b0;
+    launch_bottom(cfg(1, w.fp64, s), A, T, N, lmin, ltop, top, mode, w.u->p, w.rho->p, w.vold->p, o.n_down, o.n_up,
                   o.n_base, hom, b0);
 }
 
 // FAS V-cycle (Sec. 3.2) from ltop down to the coarsest grid and back.  The
-// levels at and below the root box run in one launch (k_bottom).
+// levels at and below btop(w) (the root box, or level 2 of a one-root tree)
+// run in one launch (k_bottom).
 void Grid::vcycle(Workspace &w, int ltop, const MgOpts &o, int hom, const int *active, cudaStream_t s) {
     if (levels_path()) {
         vcycle_levels(w, ltop, o, hom, active, s);
         return;
     }
-    for (int l = ltop; l > 1; --l) {
+    const int top = btop(w);
+    for (int l = ltop; l > top; --l) {
         smooth(w, l, o.n_down, hom, active, s);
         down_step(w, l, hom, active, s);
     }
-    bottom(w, ltop < 1 ? ltop : 1, 0, o, hom, active, s);
-    for (int l = 2; l <= ltop; ++l) {
+    bottom(w, ltop < top ? ltop : top, 0, o, hom, active, s);
+    for (int l = top + 1; l <= ltop; ++l) {
         correct(w, l, active, s);
         smooth(w, l, o.n_up, hom, active, s);
     }
@@ -468,10 +478,11 @@ void Grid::fmg(Workspace &w, const MgOpts &o, int hom, bool masked, cudaStream_t
     for (int l = lmax; l > lmin; --l) restrict_u(w, l, L(l).b0, L(l).nb, nullptr, s);
     for (int l = lmax; l > lmin; --l) down_step(w, l, hom, nullptr, s);
     const size_t es = w.fp64 ? 8 : 4;
-    // steps l = lmin..1 in one launch (every tree reaches level 1)
+    // steps l = lmin..btop in one launch (every tree reaches level btop)
+    const int l0 = levels_path() ? 1 : btop(w);
     if (levels_path()) fmg_low_levels(w, o, hom, s);
-    else bottom(w, 1, 1, o, hom, nullptr, s);
-    for (int l = 2; l <= lmax; ++l) {
+    else bottom(w, l0, 1, o, hom, nullptr, s);
+    for (int l = l0 + 1; l <= lmax; ++l) {
         Level &v = L(l);
         const int *active = masked ? fmg_mask(l) : nullptr;
         check(cudaMemcpyAsync((char *)w.vold->p + v.c0 * es, (char *)w.u->p + v.c0 * es, v.ncell * es,

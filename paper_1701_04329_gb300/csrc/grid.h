@@ -91,6 +91,13 @@ class Grid {
     // a single tree whose level 1 is a block of root boxes: no device boxes
     // below level 1 (the block bottom solve keeps those grids in shared memory)
     bool block = false;
+    // highest level of the bottom launch (k_bottom) per precision: 1, or 2
+    // for one tree of one root box whose level-2 grid fits one CTA's shared
+    // memory (FP32), and in FP64 only while that grid holds at most 1024
+    // cells (one SM's FP64 rate makes a larger one slower there than the
+    // per-level kernels: 130 us per call for 16^3 against about 110 us)
+    int btop32 = 1, btop64 = 1;
+    int btop(const Workspace &w) const { return w.fp64 ? btop64 : btop32; }
     int block_nroot[3] = {1, 1, 1}, block_bct[6] = {0, 0, 0, 0, 0, 0};
     int *d_root_box = nullptr;  // box id of root ri + nroot0 (rj + nroot1 rk)
     std::vector<Level> lv;

@@ -41,13 +41,20 @@ size_t max_smem_optin() { return (size_t)device_attr(cudaDevAttrMaxSharedMemoryP
 int occupancy(const void *kernel, size_t smem) {
     static std::mutex mu;
     static std::map<std::tuple<int, const void *, size_t>, int> cache;  // per device: the attribute is too
+    // the shared-memory limit set so far per kernel: it only grows, so that a
+    // launch with less shared memory never lowers it under a larger one
+    static std::map<std::pair<int, const void *>, size_t> limit;
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     auto key = std::make_tuple(dev, kernel, smem);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t &lim = limit[std::make_pair(dev, kernel)];
+    if (smem > 48 * 1024 && smem > lim) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        lim = smem;
+    }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem) != cudaSuccess || occ < 1) occ = 1;
     cache[key] = occ;
@@ -57,9 +64,13 @@ int occupancy(const void *kernel, size_t smem) {
 #define AFG_BY_DIM(FN, ...) \
     do { if (c.D == 2) DimOps<2>::FN(__VA_ARGS__); else DimOps<3>::FN(__VA_ARGS__); } while (0)
 
-void launch_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode, void *u,
-                   void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
-    AFG_BY_DIM(bottom, c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+void launch_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int top, int mode,
+                   void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    AFG_BY_DIM(bottom, c, A, ntrees, N, lmin, ltop, top, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+}
+size_t bottom_smem(int D, bool fp64, int top_m) {
+    if (D == 2) return fp64 ? bottom_smem<2, double>(top_m) : bottom_smem<2, float>(top_m);
+    return fp64 ? bottom_smem<3, double>(top_m) : bottom_smem<3, float>(top_m);
 }
 void launch_bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct, const int *root_box,
                          int N, int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom) {

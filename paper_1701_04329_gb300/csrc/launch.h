@@ -25,11 +25,15 @@ struct LaunchCfg {
 // counts launches of this library's kernels (host side)
 extern unsigned long long g_launches;
 
-// the levels at and below the root box in one launch (one CTA per tree):
-// mode 0 = V-cycle from ltop (<= 1), mode 1 = the FMG steps up to level 1;
-// lvl_b0[li] = first box of level lmin + li
-void launch_bottom(const LaunchCfg &, const BoxMeta &, int ntrees, int N, int lmin, int ltop, int mode, void *u,
-                   void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+// the levels at and below the root box in one launch (one CTA per tree), and
+// level 2 as well for one tree of one root box (top = 2; otherwise top = 1):
+// mode 0 = V-cycle from ltop (<= top), mode 1 = the FMG steps up to level
+// top; lvl_b0[li] = first box of level lmin + li (li = 0 .. top - lmin)
+constexpr int kBottomLevels = 6;  // grids of 2 .. 64 cells per side
+void launch_bottom(const LaunchCfg &, const BoxMeta &, int ntrees, int N, int lmin, int ltop, int top, int mode,
+                   void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
+// shared memory of that launch for grids of up to top_m cells per side (bytes)
+size_t bottom_smem(int D, bool fp64, int top_m);
 // the levels at and below level 1 of one tree whose level 1 is a block of
 // root boxes (one CTA): nroot[3] roots per axis, bct[6] side types,
 // root_box (device) the box id of root ri + nroot0 (rj + nroot1 rk); mode 0 =

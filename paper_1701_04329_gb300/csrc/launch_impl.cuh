@@ -34,10 +34,10 @@ int grid_for(K kernel, size_t smem, int work_ctas) {
 // while its predecessor drains; every kernel waits (griddepcontrol.wait)
 // before reading data a predecessor wrote.
 template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s, Args... args) {
+void launch_pdl_block(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -46,6 +46,11 @@ void launch_pdl(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s, Args... args) {
+    launch_pdl_block(kernel, grid, kThreads, smem, s, args...);
 }
 
 template <int D, int M>
@@ -277,15 +282,27 @@ void do_rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, co
     ++g_launches;
 }
 
+static_assert(kBottomLevels == kBottomMaxLevels, "bottom level count");
+
 template <int D, typename T>
-void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode, void *u,
-               void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
-    const size_t smem = bottom_smem<D, T>(N);
+void do_bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int top, int mode,
+               void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    const size_t smem = bottom_smem<D, T>(top == 2 ? 2 * N : N);
     auto k = k_bottom<D, T>;
-    occupancy(reinterpret_cast<const void *>(k), smem);  // sets the shared-memory limit once
-    const int4 b0 = make_int4(lvl_b0[0], lvl_b0[1], lvl_b0[2], lvl_b0[3]);
-    launch_pdl(k, ntrees, smem, c.stream, A, ntrees, N, lmin, ltop, mode, (T *)u, (T *)rho, (T *)vold, nd, nu, nb,
-               hom, b0);
+    occupancy(reinterpret_cast<const void *>(k), smem);  // sets the shared-memory limit
+    BottomArgs P = {};
+    P.ntrees = ntrees;
+    P.N = N;
+    P.lmin = lmin;
+    P.ltop = ltop;
+    P.mode = mode;
+    P.nd = nd;
+    P.nu = nu;
+    P.nb = nb;
+    P.hom = hom;
+    P.top = top;
+    for (int li = 0; li <= top - lmin && li < kBottomMaxLevels; ++li) P.b0[li] = lvl_b0[li];
+    launch_pdl_block(k, ntrees, kBottomThreads, smem, c.stream, A, P, (T *)u, (T *)rho, (T *)vold);
     ++g_launches;
 }
 
@@ -343,7 +360,7 @@ void do_bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, con
 template <int D, typename T>
 struct PrecOps {
     static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh);
-    static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
+    static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int top, int mode,
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
     static void bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct,
                              const int *root_box, int N, int mode, void *u, void *rho, void *vold, int nd, int nu,
@@ -369,9 +386,10 @@ void PrecOps<D, T>::rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *lis
 }
 
 template <int D, typename T>
-void PrecOps<D, T>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
-                           void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
-    do_bottom<D, T>(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+void PrecOps<D, T>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int top,
+                           int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom,
+                           const int *lvl_b0) {
+    do_bottom<D, T>(c, A, ntrees, N, lmin, ltop, top, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
 }
 
 template <int D, typename T>
@@ -429,7 +447,7 @@ void PrecOps<D, T>::leaf_get(const LaunchCfg &c, const BoxMeta &A, const int *li
 template <int D>
 struct DimOps {
     static void rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, int n, const void *rho, void *rhoh);
-    static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
+    static void bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int top, int mode,
                        void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0);
     static void bottom_block(const LaunchCfg &c, const BoxMeta &A, const int *nroot, const int *bct,
                              const int *root_box, int N, int mode, void *u, void *rho, void *vold, int nd, int nu,
@@ -468,10 +486,12 @@ void DimOps<D>::rho_hat(const LaunchCfg &c, const BoxMeta &A, const int *list, i
 }
 
 template <int D>
-void DimOps<D>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int mode,
-                       void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
-    if (c.fp64) PrecOps<D, double>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
-    else PrecOps<D, float>::bottom(c, A, ntrees, N, lmin, ltop, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+void DimOps<D>::bottom(const LaunchCfg &c, const BoxMeta &A, int ntrees, int N, int lmin, int ltop, int top,
+                       int mode, void *u, void *rho, void *vold, int nd, int nu, int nb, int hom, const int *lvl_b0) {
+    if (c.fp64)
+        PrecOps<D, double>::bottom(c, A, ntrees, N, lmin, ltop, top, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
+    else
+        PrecOps<D, float>::bottom(c, A, ntrees, N, lmin, ltop, top, mode, u, rho, vold, nd, nu, nb, hom, lvl_b0);
 }
 
 template <int D>
