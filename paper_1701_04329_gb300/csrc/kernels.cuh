@@ -452,11 +452,18 @@ __device__ __forceinline__ T nb_sum_x(const T (&x)[2 * D]) {
 }
 
 // the same less 2D times the centre value c: h^2 times the operator of Eq. 5
+// (FP64: -2D c joins the exact sum of the first kFxTerms neighbours, so the
+// FP64 pipe adds only the remaining neighbours)
 template <int D, typename T, bool FX = true>
 __device__ __forceinline__ T nb_lap_x(T c, const T (&x)[2 * D]) {
-    if constexpr (FX && kFxTerms >= 2 * D && sizeof(T) == 8) {
+    if constexpr (FX && sizeof(T) == 8) {
+        constexpr int K = kFxTerms < 2 * D ? kFxTerms : 2 * D;
         double s;
-        if (fx_sum<2 * D, 2 * D>(x, c, s)) return s;
+        if (fx_sum<K, 2 * D>(x, c, s)) {
+#pragma unroll
+            for (int k = K; k < 2 * D; ++k) s += x[k];
+            return s;
+        }
     }
     return fma(T(-2 * D), c, nb_sum_x<D, T, FX>(x));
 }
