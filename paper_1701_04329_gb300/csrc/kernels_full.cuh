@@ -118,6 +118,110 @@ __device__ __forceinline__ void fp_issue(const BoxInfo &I, const T *u, const T *
     }
 }
 
+// Per-thread copy plan of fp_issue, the same for every box of a launch: for
+// each ghost item of the thread, the destination in the stage, the side,
+// whether it is a scalar (x side), the source offsets relative to the
+// neighbour box (same-level copy) and to the box itself (the mirror u_1),
+// and the item's first boundary-data offset (stride 2 along a y/z item).
+template <int D, int M, typename T, int GT>
+struct FpPlan {
+    using F = FpCfg<D, M, T, GT>;
+    static constexpr int NIV = (F::NV + F::G - 1) / F::G;
+    static constexpr int NQ = (F::NGI + F::G - 1) / F::G;
+    int vdst[NIV];
+    int gdst[NQ], gsrc[NQ], gbc[NQ];  // dst | side << 16 | scalar << 19 ; copy | mirror << 16
+    __device__ __forceinline__ void init(int lt) {
+        constexpr int VEC = F::VEC, MH = F::MH, H = F::H, NVH = H / VEC;
+#pragma unroll
+        for (int it = 0; it < NIV; ++it) {
+            const int v = lt + it * F::G;
+            const int col = v / NVH, w = v % NVH;
+            const int row = w / F::NVR, h0 = (w % F::NVR) * VEC;
+            const int j = row % M, k = D == 2 ? 0 : row / M;
+            vdst[it] = v < F::NV ? col * F::PT + sp_row<D, M>(j, k) * MH + h0 : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int item = lt + q * F::G;
+            gdst[q] = -1;
+            gsrc[q] = gbc[q] = 0;
+            if (item >= F::NGI) continue;
+            if (item < F::NXI) {
+                int s, j, k;
+                fp_xitem<D, M>(item, s, j, k);
+                const int colg = ((s ? M : -1) + j + k + D) & 1;  // colour of the ghost cell
+                gdst[q] = (2 * F::PT + s * F::ROWS + sp_row<D, M>(j, k)) | (s << 16) | (1 << 19);
+                gsrc[q] = (colg * H + hrow<D, M>(j, k) + (s ? 0 : MH - 1)) |
+                          (((1 - colg) * H + hrow<D, M>(j, k) + (s ? MH - 1 : 0)) << 16);
+                gbc[q] = k * M + j;
+            } else {
+                int s, col, h0, jg, kg, jin, kin, jm, km;
+                fp_yzitem<D, M, T>(item - F::NXI, s, col, h0, jg, kg, jin, kin, jm, km);
+                gdst[q] = (col * F::PT + sp_row<D, M>(jg, kg) * MH + h0) | (s << 16);
+                gsrc[q] = (col * H + hrow<D, M>(jm, km) + h0) | (((1 - col) * H + hrow<D, M>(jin, kin) + h0) << 16);
+                const int rg = (col + jg + kg + D) & 1;
+                gbc[q] = ((s >> 1) == 1 ? kin : jin) * M + 2 * h0 + rg;
+            }
+        }
+    }
+};
+
+// fp_issue through the plan
+template <int D, int M, typename T, int GT>
+__device__ __forceinline__ void fp_issue_plan(const FpPlan<D, M, T, GT> &pl, const BoxInfo &I, const T *u,
+                                              const T *flat, T *st, int lt, bool image) {
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC;
+    const T *ub = u + I.coff;
+    T *fl = st + F::UB;
+#pragma unroll
+    for (int it = 0; it < FpPlan<D, M, T, GT>::NIV; ++it) {
+        const int v = lt + it * F::G;
+        if (pl.vdst[it] < 0) continue;
+        if (image) cp_async<16>(st + pl.vdst[it], ub + v * VEC);
+        if (flat) cp_async<16>(fl + v * VEC, flat + I.coff + v * VEC);
+    }
+    if (!image) return;
+#pragma unroll
+    for (int q = 0; q < FpPlan<D, M, T, GT>::NQ; ++q) {
+        const int dst = pl.gdst[q];
+        if (dst < 0) continue;
+        const int sd = (dst >> 16) & 7;
+        const T *src = I.code[sd] >= 0 ? u + I.base[sd] + (pl.gsrc[q] & 0xffff) : ub + (pl.gsrc[q] >> 16);
+        if (dst & (1 << 19)) cp_async<(int)sizeof(T)>(st + (dst & 0xffff), src);
+        else cp_async<16>(st + (dst & 0xffff), src);
+    }
+}
+
+// fp_fix_own through the plan
+template <int D, int M, typename T, int GT>
+__device__ __forceinline__ void fp_fix_own_plan(const FpPlan<D, M, T, GT> &pl, const BoxInfo &I, const BoxMeta &A,
+                                                T *st, int hom) {
+    using F = FpCfg<D, M, T, GT>;
+    constexpr int VEC = F::VEC;
+#pragma unroll
+    for (int q = 0; q < FpPlan<D, M, T, GT>::NQ; ++q) {
+        const int dst = pl.gdst[q];
+        if (dst < 0) continue;
+        const int sd = (dst >> 16) & 7;
+        if (I.code[sd] != -1) continue;
+        const bool neu = (I.nmask >> sd) & 1;
+        const T hbox = neu ? T(A.hb[I.b]) : T(0);
+        const double *bc = A.bc + I.base[sd] + pl.gbc[q];
+        T *gv = st + (dst & 0xffff);
+        if (dst & (1 << 19)) {
+            const T bv = hom ? T(0) : T(bc[0]);
+            gv[0] = neu ? fma(hbox, bv, gv[0]) : T(2) * bv - gv[0];
+        } else {
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) {
+                const T bv = hom ? T(0) : T(bc[2 * x]);
+                gv[x] = neu ? fma(hbox, bv, gv[x]) : T(2) * bv - gv[x];
+            }
+        }
+    }
+}
+
 // Completes the domain-side ghosts among this thread's own items (the ones
 // fp_issue gave it) from the u_1 it staged there: 2 b - u_1 (Dirichlet) or
 // u_1 + h b (Neumann).  Its own copies are visible to it after its wait, so
@@ -259,8 +363,10 @@ __device__ __forceinline__ void fp_lap_vec(const T *st, int col, int j, int k, i
 // OWN: the issuing threads complete the domain-side ghosts before the box's
 // barrier (fp_fix_own) and only refinement-boundary boxes take the extra
 // barrier; otherwise every box with a non-copy side takes it (fewer registers).
-template <int D, int M, typename T, int GT, bool OWN = true, typename Want, typename Flat, typename Body, typename Pre,
-          typename Post>
+// PLAN: copies and domain-side fixes through a per-thread plan (FpPlan), no
+// per-box decoding of the items (more registers).
+template <int D, int M, typename T, int GT, bool OWN = true, bool PLAN = false, typename Want, typename Flat,
+          typename Body, typename Pre, typename Post>
 __device__ __forceinline__ void fp_walk(const BoxMeta &A, int b0, int n, const int *list, const T *u, int hom,
                                         Want want, Flat flat, Body body, Pre pre, Post post) {
     using F = FpCfg<D, M, T, GT>;
@@ -276,9 +382,15 @@ __device__ __forceinline__ void fp_walk(const BoxMeta &A, int b0, int n, const i
     pdl_wait();
     for (int q = 0; q < NST; ++q) info_mask<D>(A, info[q * F::BPC + g], lt, F::G);
     __syncthreads();
+    FpPlan<D, M, T, GT> pl;
+    if constexpr (PLAN) pl.init(lt);
     auto issue = [&](int q) {
         const BoxInfo &In = info[(q % NI) * F::BPC + g];
-        if (In.b >= 0) fp_issue<D, M, T, GT>(In, u, flat(In), stages + ((q % NST) * F::BPC + g) * F::BOX, lt, want(In));
+        T *dst = stages + ((q % NST) * F::BPC + g) * F::BOX;
+        if (In.b >= 0) {
+            if constexpr (PLAN) fp_issue_plan<D, M, T, GT>(pl, In, u, flat(In), dst, lt, want(In));
+            else fp_issue<D, M, T, GT>(In, u, flat(In), dst, lt, want(In));
+        }
         cp_commit();
     };
     for (int q = 0; q < NST - 1; ++q) issue(q);
@@ -289,7 +401,10 @@ __device__ __forceinline__ void fp_walk(const BoxMeta &A, int b0, int n, const i
         const bool special = I.b >= 0 && want(I) && (I.flag & BF_SPECIAL);
         const bool cf = special && (!OWN || (I.flag & BF_CF));
         T *st = stages + ((it % NST) * F::BPC + g) * F::BOX;
-        if (OWN && special) fp_fix_own<D, M, T, GT>(I, A, st, lt, hom);  // domain sides: this thread's own items
+        if (OWN && special) {  // domain sides: this thread's own items
+            if constexpr (PLAN) fp_fix_own_plan<D, M, T, GT>(pl, I, A, st, hom);
+            else fp_fix_own<D, M, T, GT>(I, A, st, lt, hom);
+        }
         const int any_cf = __syncthreads_or(cf);  // previous stage and metadata slot are free now
         issue(it + NST - 1);
         info_load<D>(A, base + NST * stride + g, n, b0, list, info[((it + NST) % NI) * F::BPC + g], lt, F::G);
@@ -378,7 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_p(BoxMeta A, int b0
         }
     };
     auto none = [](const BoxInfo *) {};
-    fp_walk<D, M, T, GT>(A, b0, n, nullptr, u, hom, want, flat, body, none, none);
+    fp_walk<D, M, T, GT, true, sizeof(T) == 4>(A, b0, n, nullptr, u, hom, want, flat, body, none, none);
 }
 
 // FAS coarse right-hand side, staged version of k_fas: refined boxes get
