@@ -869,7 +869,14 @@ __global__ void __launch_bounds__(kThreads) k_rho_hat(BoxMeta A, const int *list
         const int b = list[idx];
         const long long cb = A.coff[b];
         const T c = T(-A.hb[b] * A.hb[b] / (2 * D));
-        for (int q = lt; q < Gm::C; q += Gm::G) rhoh[cb + q] = c * rho[cb + q];
+        constexpr int VEC = 16 / (int)sizeof(T);  // a box is a whole number of 16-byte vectors
+        for (int q = lt; q < Gm::C / VEC; q += Gm::G) {
+            T v[VEC];
+            ldv<T, VEC>(rho + cb + q * VEC, v);
+#pragma unroll
+            for (int x = 0; x < VEC; ++x) v[x] *= c;
+            stv<T, VEC>(rhoh + cb + q * VEC, v);
+        }
     }
 }
 
