@@ -316,7 +316,7 @@ def event_time(fn, K, W_, stream_sync=True):
 
 
 def bench_gauss2d(K, W_, dev, with_oracle):
-    """configs[0]-style 2D workload: one Gaussian, 8^2 boxes, levels 4..7;
+    """The 2D Gaussian workload: one Gaussian, 8^2 boxes, levels 4..7;
     time to 1e-8 and to 1e-10 (FP64 and mixed), graph replay on and off,
     error against the exact u and against the oracle's FP64 solution."""
     import torch
@@ -358,7 +358,7 @@ def bench_gauss2d(K, W_, dev, with_oracle):
 
 
 def bench_blobs3d(K, W_, dev):
-    """configs[4]-style differentiable 3D workload (uniform 128^3 + 1 level,
+    """The differentiable 3D workload (uniform 128^3 + 1 level,
     8 Gaussian blobs): the forward solve and the backward (adjoint) solve
     through torch.autograd, to 1e-10 each."""
     import torch
@@ -424,7 +424,7 @@ def bench_paper_cmp(K, W_, dev):
 
 
 def bench_forest(K, W_, dev, hbm, dist=None, rank=0, world=1):
-    """configs[3]-style batched workload at the tuner's recorded choice: 512
+    """The batched workload at the tuner's recorded choice: 512
     quadtrees (seeds 1000+t), mixed precision to 1e-8 per tree, CUDA-graph
     replay; unknowns/s and the roofline of its FP32 half-sweep.  With N
     ranks the trees are split by LPT on box count (paper_1701_04329_gb300/
