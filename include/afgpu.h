@@ -73,9 +73,11 @@ typedef struct {
     int max_cycles;    /* cycle limit for afg_solve / adjoint iterations (default 50) */
     double rel_tol;    /* stop when max|rho - A u| / max|rho| <= rel_tol (default 1e-10) */
     int precision;     /* AFG_FP64 or AFG_MIXED */
-    int inner_vcycles; /* AFG_MIXED: FP32 V-cycles per outer FP64 step after the first (FMG) step
-                          (default 2: each FP64 residual pass, FP64-arithmetic bound, then buys two
-                          V-cycles of reduction; 1 gives the plain alternation) */
+    int inner_vcycles; /* AFG_MIXED: FP32 V-cycles per outer FP64 step after the first (FMG) step,
+                          1..16; 0 (default): for one tree, 2 on the first such step, then
+                          chosen per step from the reduction per V-cycle measured on the step
+                          before so that the step reaches rel_tol, at most a factor 1e-5 per
+                          step (the FP32 solve's resolution); for forests, 2 */
     int use_graph;     /* 1: replay the cycle as a CUDA graph (default 1) */
     int threads_per_box; /* FP32 half-sweep (the mixed-precision solves): threads per box, 0 (default) or
                             one per 16-byte vector of a box's colour half, min(N^D/8, 256), or half as

@@ -114,7 +114,7 @@ int validate(const afg_mg_opts &o) {
         return fail(AFG_ERR_ARG, "smoothing steps out of range");
     if (o.max_cycles < 1 || !(o.rel_tol >= 0.0)) return fail(AFG_ERR_ARG, "bad max_cycles / rel_tol");
     if (o.precision != AFG_FP64 && o.precision != AFG_MIXED) return fail(AFG_ERR_ARG, "bad precision");
-    if (o.inner_vcycles < 1 || o.inner_vcycles > 16) return fail(AFG_ERR_ARG, "inner_vcycles out of range");
+    if (o.inner_vcycles < 0 || o.inner_vcycles > 16) return fail(AFG_ERR_ARG, "inner_vcycles out of range");
     if (o.threads_per_box < 0) return fail(AFG_ERR_ARG, "threads_per_box out of range");
     return AFG_OK;
 }
@@ -238,16 +238,44 @@ int solve_mixed(Grid &g, const afg_mg_opts &o, cudaStream_t s, std::vector<std::
     };
     run(g, {10, 0, 0, 0, 0}, o.use_graph, s, residual);
     check(cudaStreamSynchronize(s), "solve");
+    // inner_vcycles 0, one tree: two V-cycles on the first step after FMG, then
+    // as many as the reduction per V-cycle measured on the previous step says
+    // reach the tolerance in this step (the FP64 residual passes are then as
+    // few as the FP32 resolution allows); forests: two (trees converge at
+    // different rates, and every active tree would take the worst one's count)
+    auto worst = [&]() {
+        double r = 0;
+        for (int t = 0; t < g.T; ++t)
+            if (!hist[t].empty() && hist[t].back() > o.rel_tol) r = std::max(r, hist[t].back());
+        return r;
+    };
+    double rate = 0, r_prev = 0;  // reduction per V-cycle, measured
+    int k_prev = 0;
     int cycles = 0;
     while (*g.h_nactive > 0 && cycles < o.max_cycles) {
         const bool first = cycles == 0;
-        run(g, {first ? 11 : 12, o.n_down, o.n_up, o.n_base, o.inner_vcycles}, o.use_graph, s,
+        int k = o.inner_vcycles;
+        if (!first && k == 0) {
+            const double r = worst();
+            if (k_prev > 0 && r_prev > 0 && r > 0)
+                rate = std::min(0.5, std::max(0.01, std::pow(r / r_prev, 1.0 / k_prev)));
+            k = 2;
+            if (!forest && rate > 0) {
+                const double need = r > o.rel_tol ? std::log(r / o.rel_tol) / -std::log(rate) : 1.0;
+                // at most 1e-5 per pass: the FP32 solve's resolution bounds what one pass can gain
+                const int kmax = std::max(1, (int)std::floor(std::log(1e-5) / std::log(rate)));
+                k = std::min(kmax, std::max(1, (int)std::ceil(need - 1e-9)));
+            }
+            r_prev = r;
+            k_prev = k;
+        }
+        run(g, {first ? 11 : 12, o.n_down, o.n_up, o.n_base, k}, o.use_graph, s,
             [&](cudaStream_t cs) {
                 const int *active = forest ? g.d_converged_mask() : nullptr;
                 check(cudaMemsetAsync(g.ws32.u->p, 0, bytes32, cs), "zero e");
                 if (first) g.fmg(g.ws32, mo, 1, forest, cs);
                 else
-                    for (int k = 0; k < o.inner_vcycles; ++k) g.vcycle(g.ws32, g.lmax, mo, 1, active, cs);
+                    for (int q = 0; q < k; ++q) g.vcycle(g.ws32, g.lmax, mo, 1, active, cs);
                 afg::BoxMeta A = g.meta;
                 A.active = active;
                 afg::launch_mixed_update(g.leaf_cfg(true, cs), A, g.d_leaves, g.n_leaf_boxes, g.ws64.u->as<double>(),
@@ -376,7 +404,7 @@ void afg_default_opts(afg_mg_opts *o) {
     o->max_cycles = 50;
     o->rel_tol = 1e-10;
     o->precision = AFG_FP64;
-    o->inner_vcycles = 2;
+    o->inner_vcycles = 0;
     o->use_graph = 1;
     o->threads_per_box = 0;
 }

@@ -92,6 +92,25 @@ def test_mixed_precision_matches_fp64_oracle():
     assert rel_diff(b.get_solution(), a.get_solution()) <= 1e-8
 
 
+@pytest.mark.parametrize("inner", [0, 1, 3])
+def test_mixed_precision_inner_cycles(inner):
+    """A fixed number of FP32 V-cycles per FP64 step, and the default (chosen
+    per step from the measured reduction), all reach the tolerance and the
+    FP64 oracle's solution."""
+    a, b, rho, bv = pair_from_problem(W.twosrc3d(uniform_level=4, extra_levels=2, s=0.04))
+    load(a, b, rho, bv)
+    a.solve(1e-12, 60)
+    opts = afgpu.default_opts(rel_tol=1e-10, precision=afgpu.AFG_MIXED)
+    assert opts.inner_vcycles == 0
+    opts.inner_vcycles = inner
+    sb = b.solve(opts)
+    assert sb["rel_residual"] <= 1e-10
+    assert rel_diff(b.get_solution(), a.get_solution()) <= 1e-8
+    opts.inner_vcycles = 17
+    with pytest.raises(afgpu.AfgError):
+        b.solve(opts)
+
+
 def test_empty_rhs_and_errors():
     t = afgpu.Tree(2, 8, 3)
     t.refine_uniform(2)
