@@ -144,11 +144,13 @@ int afg_tree_create(int dim, int box_n, int max_level, afg_tree **out);
  * (x (r_z M + 2)) values plus the face data of the non-periodic sides -- up
  * to 8 x 8 roots of 8^2 boxes, 4 x 4 of 16^2, 6 x 1 x 1 or 3 x 2 x 1 of 8^3,
  * no block of 16^3 boxes) solves them in that CTA, one launch per cycle;
- * larger blocks, and every tree of a forest that holds a block tree, run
- * them as device boxes through the per-level kernels, like the finer levels.
- * The variable-coefficient operators and the other prolongations take trees
- * of one root box (AFG_ERR_ARG); singular problems too.  AFG_ERR_ARG when
- * nroot[a] << (max_level-1) exceeds 2^21. */
+ * larger blocks, every tree of a forest that holds a block tree, and a tree
+ * given a variable-coefficient operator or another prolongation before its
+ * data (afg_set_operator, afg_set_prolongation; afterwards AFG_ERR_STATE
+ * where the block solve was chosen) run them as device boxes through the
+ * per-level kernels, like the finer levels.  Singular problems take trees
+ * of one root box.  AFG_ERR_ARG when nroot[a] << (max_level-1) exceeds
+ * 2^21. */
 int afg_tree_create_roots(int dim, int box_n, int max_level, const int *nroot, afg_tree **out);
 int afg_tree_destroy(afg_tree *t);
 
@@ -263,8 +265,9 @@ int afg_set_dirichlet(afg_tree *t, const double *b_face_dev);
  * stays the normal derivative of u (flux eps b).  The coarse-grid correction
  * keeps the linear prolongation.  Host call; changing it keeps the field data
  * but requires afg_set_eps again.  AFG_ERR_ARG for an unknown op, (r,z) on a
- * 3D tree or with a periodic -x side, and for trees of several root boxes.
- * Not covered with these operators: afg_adjoint and
+ * 3D tree or with a periodic -x side; AFG_ERR_STATE on a tree of several
+ * root boxes whose data were set for the one-CTA block solve (set the
+ * operator first).  Not covered with these operators: afg_adjoint and
  * afg_forest_residual_norms_noalloc (AFG_ERR_STATE), afg_time_kernel. */
 #define AFG_OP_LAPLACE 0
 #define AFG_OP_VAR 1
@@ -278,8 +281,9 @@ int afg_set_operator(afg_tree *t, int op);
  * from the diagonal same-level neighbour, else extrapolated linearly) or
  * AFG_PROLONG_ZEROTH (the coarse cell's value).  With a non-default scheme
  * every level, the coarse grids below the root included, runs on the
- * per-level kernels.  Host call; AFG_ERR_ARG for an unknown scheme or a tree
- * of several root boxes. */
+ * per-level kernels.  Host call; AFG_ERR_ARG for an unknown scheme;
+ * AFG_ERR_STATE on a tree of several root boxes whose data were set for the
+ * one-CTA block solve (set the scheme first). */
 #define AFG_PROLONG_LINEAR 0
 #define AFG_PROLONG_MULTILINEAR 1
 #define AFG_PROLONG_ZEROTH 2

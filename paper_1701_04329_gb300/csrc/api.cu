@@ -123,7 +123,7 @@ Grid &grid_of(afg_tree *t) {
     if (!t->grid || t->grid_version != t->ht.version) {
         t->grid.reset();
         std::vector<const HostTree *> v{&t->ht};
-        t->grid.reset(new Grid(v));
+        t->grid.reset(new Grid(v, t->op || t->prolong));
         t->grid_version = t->ht.version;
         t->grid->op = t->op;
         t->grid->prolong = t->prolong;
@@ -556,7 +556,7 @@ int afg_adapt_transfer(afg_tree *t, const int8_t *flags, int n_buf, int scheme, 
     std::unique_ptr<Grid> fresh;
     {
         std::vector<const HostTree *> v{&t->ht};
-        fresh.reset(new Grid(v));
+        fresh.reset(new Grid(v, t->op || t->prolong));
         fresh->op = t->op;
         fresh->prolong = t->prolong;
     }
@@ -678,7 +678,8 @@ int afg_set_operator(afg_tree *t, int op) {
     if (!t) return fail(AFG_ERR_ARG, "null tree");
     if (op < 0 || op > 2) return fail(AFG_ERR_ARG, "op must be AFG_OP_LAPLACE, AFG_OP_VAR or AFG_OP_VAR_RZ");
     if (op == 2 && t->ht.D != 2) return fail(AFG_ERR_ARG, "(r,z) coordinates need a 2D tree");
-    if (op && t->ht.nroots() != 1) return fail(AFG_ERR_ARG, "the variable-coefficient operators need a single root box");
+    if (op && t->grid && t->grid->block)
+        return fail(AFG_ERR_STATE, "a tree of several root boxes takes its operator before its data");
     if (op == 2 && t->ht.bct[0] == 2) return fail(AFG_ERR_ARG, "(r,z): the -x side is the axis and cannot be periodic");
     bool dir = false;
     for (int s2 = 0; s2 < 2 * t->ht.D; ++s2) dir |= t->ht.bct[s2] == 0;
@@ -698,7 +699,8 @@ int afg_set_operator(afg_tree *t, int op) {
 int afg_set_prolongation(afg_tree *t, int scheme) {
     if (!t) return fail(AFG_ERR_ARG, "null tree");
     if (scheme < 0 || scheme > 2) return fail(AFG_ERR_ARG, "scheme must be AFG_PROLONG_LINEAR, _MULTILINEAR or _ZEROTH");
-    if (scheme && t->ht.nroots() != 1) return fail(AFG_ERR_ARG, "other prolongations need a single root box");
+    if (scheme && t->grid && t->grid->block)
+        return fail(AFG_ERR_STATE, "a tree of several root boxes takes its prolongation before its data");
     AFG_API_BEGIN
     t->prolong = scheme;
     if (t->grid) {

@@ -80,7 +80,7 @@ T *upload(const std::vector<T> &v, std::vector<std::unique_ptr<DevBuf>> &owned) 
 }
 }  // namespace
 
-Grid::Grid(const std::vector<const HostTree *> &trees) {
+Grid::Grid(const std::vector<const HostTree *> &trees, bool levels_only) {
     device = current_device();
     D = trees[0]->D;
     N = trees[0]->N;
@@ -94,7 +94,7 @@ Grid::Grid(const std::vector<const HostTree *> &trees) {
     // tree, in one launch per cycle (k_bottom).
     bool multi = false;
     for (const HostTree *h : trees) multi |= h->nroots() != 1;
-    block = T == 1 && multi &&
+    block = T == 1 && multi && !levels_only &&
             bottom_block_smem(D, true, N, trees[0]->nr, trees[0]->bct) <= max_smem_optin();
     roots_levels = multi && !block;
     for (const HostTree *h : trees) {

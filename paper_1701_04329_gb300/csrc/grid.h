@@ -74,7 +74,10 @@ struct MgOpts {
 
 class Grid {
   public:
-    explicit Grid(const std::vector<const HostTree *> &trees);
+    // levels_only: a tree of several root boxes keeps its coarse grids as
+    // device boxes (the per-level kernels) even where they fit one CTA (the
+    // variable-coefficient operators and the other prolongations run there)
+    explicit Grid(const std::vector<const HostTree *> &trees, bool levels_only = false);
     ~Grid();
     int device = 0;  // the CUDA device holding this grid's data
 

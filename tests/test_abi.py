@@ -119,8 +119,9 @@ def test_allocator_needs_both_callbacks():
 
 
 def test_operator_validated_on_the_host():
-    """afg_set_operator: known operators only, (r,z) in 2D only, single root
-    box; eps needs a variable-coefficient operator first (no GPU needed)."""
+    """afg_set_operator: known operators only, (r,z) in 2D only; a tree of
+    several root boxes takes it before its data; eps needs a
+    variable-coefficient operator first (no GPU needed)."""
     t = afgpu.Tree(3, 8, 2)
     for bad in (3, -1, afgpu.AFG_OP_VAR_RZ):
         try:
@@ -129,11 +130,8 @@ def test_operator_validated_on_the_host():
         except afgpu.AfgError as e:
             assert e.code == afgpu.AFG_ERR_ARG
     m = afgpu.Tree(2, 8, 2, roots=(2, 1))
-    try:
-        m.set_operator(afgpu.AFG_OP_VAR)
-        assert False
-    except afgpu.AfgError as e:
-        assert e.code == afgpu.AFG_ERR_ARG
+    m.set_operator(afgpu.AFG_OP_VAR)  # no data yet: the coarse grids go to the per-level kernels
+    m.set_prolongation(afgpu.AFG_PROLONG_MULTILINEAR)
     L = afgpu.lib()
     assert L.afg_set_eps(t._h, ctypes.c_void_p(8)) == afgpu.AFG_ERR_STATE
     afgpu.Tree(2, 8, 2).set_operator(afgpu.AFG_OP_VAR_RZ)

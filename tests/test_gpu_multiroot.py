@@ -73,15 +73,43 @@ def test_block_solve_and_mixed_precision(D):
     assert rel_diff(b.get_solution(), a.get_solution()) <= 1e-8
 
 
+@pytest.mark.parametrize("D,roots,op,scheme,seed", [
+    (2, (2, 1), afgpu.AFG_OP_VAR, 0, 640), (2, (3, 2), afgpu.AFG_OP_VAR_RZ, 0, 641),
+    (2, (1, 3), 0, afgpu.AFG_PROLONG_MULTILINEAR, 642), (3, (2, 1, 1), afgpu.AFG_OP_VAR, 0, 643),
+    (3, (1, 2, 1), 0, afgpu.AFG_PROLONG_ZEROTH, 644), (2, (2, 2), afgpu.AFG_OP_VAR, afgpu.AFG_PROLONG_MULTILINEAR, 645)])
+def test_block_trees_with_other_operators_cycle_by_cycle(D, roots, op, scheme, seed):
+    """A block tree given a variable-coefficient operator (eps log-uniform in
+    [0.5, 4] per level-1 cell) or another prolongation before its data keeps
+    its coarse grids as device boxes on the per-level kernels; cycle by cycle
+    against the oracle."""
+    a, b, rho, bv = block_pair(D, 8, roots, 1, 2, seed)
+    for t in (a, b):
+        if op:
+            t.set_operator(op)
+        if scheme:
+            (t.set_prolong if t is a else t.set_prolongation)(scheme)
+    if op:
+        rng = np.random.default_rng(seed + 1)
+        x = a.cell_centers()
+        table = np.exp(rng.uniform(np.log(0.5), np.log(4.0), size=tuple(8 * r for r in roots)))
+        eps = table[tuple(np.minimum((x[:, k] * 8).astype(int), 8 * roots[k] - 1) for k in range(D))]
+        a.set_eps(eps)
+        b.set_eps(torch.tensor(eps, device="cuda"))
+    load(a, b, rho, bv)
+    cycles_parity(a, b, 2)
+
+
 def test_block_trees_refuse_what_is_not_built():
-    """The variable-coefficient operators, the other prolongations and
-    singular problems take trees of one root box."""
+    """Once the data of a block tree are set for the one-CTA block solve, the
+    operator and prolongation stay; singular problems take trees of one root
+    box."""
     t = afgpu.Tree(2, 8, 3, roots=(2, 1))
     t.refine_uniform(2)
+    t.set_rhs(torch.zeros(t.n_leaf_cells, dtype=torch.float64, device="cuda"))
     for call in (lambda: t.set_operator(afgpu.AFG_OP_VAR), lambda: t.set_prolongation(afgpu.AFG_PROLONG_ZEROTH)):
         with pytest.raises(afgpu.AfgError) as e:
             call()
-        assert e.value.code == afgpu.AFG_ERR_ARG
+        assert e.value.code == afgpu.AFG_ERR_STATE
     s = afgpu.Tree(2, 8, 3, roots=(2, 1))
     s.set_boundary_types([2, 2, 1, 1])
     s.refine_uniform(2)
