@@ -232,9 +232,10 @@ int afg_export_tree(const afg_tree *t, int32_t *level, int32_t *idx, int32_t *pa
  * A u = rho - c, c = (sum h^D rho - sum over Neumann leaf faces h^(D-1) b) /
  * sum h^D, which makes the source compatible (Sec. 4.4's gravity problem
  * subtracts the mean source), and returns the solution of zero
- * volume-weighted mean; such trees work alone (not in forests, not as blocks
- * of root boxes) with the Laplacian, and have no adjoint.  AFG_ERR_ARG for
- * any violation, with the tree unchanged.  Host call; a change discards the device fields, so set rho and
+ * volume-weighted mean (in a forest each such tree on its own: its c and its
+ * mean from its own leaves); such trees take one root box and the
+ * Laplacian, and have no adjoint.  AFG_ERR_ARG for any violation, with the
+ * tree unchanged.  Host call; a change discards the device fields, so set rho and
  * the boundary data after it.  Default: all sides Dirichlet.  Trees of a
  * forest keep the types they had when the forest was created. */
 #define AFG_BC_DIRICHLET 0

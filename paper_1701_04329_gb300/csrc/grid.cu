@@ -101,9 +101,10 @@ Grid::Grid(const std::vector<const HostTree *> &trees, bool levels_only) {
         bool dir = false;
         for (int s2 = 0; s2 < 2 * D; ++s2) dir |= h->bct[s2] == 0;
         singular |= !dir;
+        tree_sing.push_back(!dir);
     }
-    if (singular && (T > 1 || multi))
-        throw std::runtime_error("problems without a Dirichlet side are solved for single trees of one root box");
+    if (singular && multi)
+        throw std::runtime_error("problems without a Dirichlet side are solved for trees of one root box");
     int nsub = 0;
     if (!block)
         for (int m = N / 2; m >= 2; m /= 2) ++nsub;
@@ -316,6 +317,13 @@ Grid::Grid(const std::vector<const HostTree *> &trees, bool levels_only) {
     d_child = upload(child, own);
     d_leaves = upload(leaves, own);
     d_leaf_geo = upload(leaf_geo, own);
+    if (singular && T > 1) {  // forests: per-tree compatibility constants and means
+        std::vector<int> leaf0(T + 1, 0);
+        for (int t = 0; t < T; ++t) leaf0[t + 1] = leaf0[t] + (int)trees[t]->leaves.size();
+        d_tree_leaf0 = upload(leaf0, own);
+        d_tree_sing = upload(tree_sing, own);
+        d_tree_c = upload(std::vector<double>(T, 0.0), own);
+    }
     // boxes (level >= 2) whose parent has a same-level leaf across a face
     std::vector<int> cfc;
     for (auto &v : lv) {

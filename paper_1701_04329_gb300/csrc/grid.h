@@ -144,9 +144,15 @@ class Grid {
     // root and level): the cycle runs on the per-level kernels
     bool roots_levels = false;
     void correct(Workspace &w, int l, const int *active, cudaStream_t s);
-    // no Dirichlet side (single trees): the source is made compatible and the
+    // a tree without a Dirichlet side: its source is made compatible and its
     // solution kept at zero volume-weighted mean
     bool singular = false;
+    // forests: which trees are singular, each tree's first entry in d_leaves
+    // (T + 1 offsets) and its constant (the source shift, then the mean)
+    std::vector<char> tree_sing;
+    char *d_tree_sing = nullptr;
+    int *d_tree_leaf0 = nullptr;
+    double *d_tree_c = nullptr;
     void make_compatible(cudaStream_t s);
     void remove_mean(Workspace &w, cudaStream_t s);
     const void *eps_of(const Workspace &w) const { return w.fp64 ? eps64->p : eps32->p; }
@@ -199,6 +205,7 @@ void launch_cell_centers(const Grid &g, double *xyz, cudaStream_t s);
 void launch_flag(const Grid &g, const double *f, int power, double tau_ref, double tau_de, signed char *flags,
                  cudaStream_t s);
 // f -= (sum_leaves h^D f - [sum over Neumann leaf faces h^(D-1) b]) / sum h^D on the leaves
+// (forests: per singular tree, over its own leaves; other trees unchanged)
 void launch_leaf_center(const Grid &g, double *f, bool with_flux, cudaStream_t s);
 // dst = (float) src, n values
 void launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);

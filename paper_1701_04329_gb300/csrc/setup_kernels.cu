@@ -106,6 +106,45 @@ __global__ void k_leaf_shift(BoxMeta A, const int *leaves, int nleaf, int C, dou
     }
 }
 
+// Forests: block t forms tree t's constant from its own leaves, in a fixed
+// order (0 for a tree with a Dirichlet side, or one masked out by active).
+__global__ void k_tree_vsum(BoxMeta A, const int *leaves, const int *leaf0, const char *sing, const int *active,
+                            const double *geo, int D, int N, const double *f, const double *bc, double *c) {
+    __shared__ double sh[256];
+    const int t = blockIdx.x;
+    const bool on = sing[t] && (!active || active[t]);
+    const int C = D == 2 ? N * N : N * N * N, F = D == 2 ? N : N * N;
+    double sf = 0.0, sv = 0.0, sb = 0.0;
+    if (on)
+        for (int li = leaf0[t]; li < leaf0[t + 1]; ++li) {
+            const double h = geo[4 * li + 3];
+            const double vol = D == 2 ? h * h : h * h * h, area = D == 2 ? h : h * h;
+            const int b = leaves[li];
+            const long long cb = A.coff[b];
+            for (int q = threadIdx.x; q < C; q += blockDim.x) sf += vol * f[cb + q];
+            if (threadIdx.x == 0) sv += vol * C;
+            if (bc)
+                for (int s = 0; s < 2 * D; ++s)
+                    if ((A.nmask[b] >> s) & 1)
+                        for (int q = threadIdx.x; q < F; q += blockDim.x) sb += area * bc[A.bcoff[b * 2 * D + s] + q];
+        }
+    sf = block_sum(sf, sh);
+    sv = block_sum(sv, sh);
+    sb = block_sum(sb, sh);
+    if (threadIdx.x == 0) c[t] = on ? (sf - sb) / sv : 0.0;
+}
+
+// f -= c[tree] on the leaf boxes (box layout)
+__global__ void k_tree_shift(BoxMeta A, const int *leaves, int nleaf, int C, double *f, const double *c) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)nleaf * C;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int li = (int)(e / C), q = (int)(e - (long long)li * C);
+        const int b = leaves[li];
+        const double v = c[A.tree[b]];
+        if (v != 0.0) f[A.coff[b] + q] -= v;
+    }
+}
+
 __global__ void k_to_f32(const double *src, float *dst, long long n) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
         dst[q] = (float)src[q];
@@ -132,6 +171,16 @@ void launch_flag(const Grid &g, const double *f, int power, double tau_ref, doub
 // f -= (sum_leaves h^D f - [sum Neumann faces h^(D-1) b]) / sum h^D on the leaves
 void launch_leaf_center(const Grid &g, double *f, bool with_flux, cudaStream_t s) {
     if (g.n_leaf_boxes == 0) return;
+    if (g.T > 1) {  // forests: one constant per singular tree
+        const int C = g.D == 2 ? g.N * g.N : g.N * g.N * g.N;
+        k_tree_vsum<<<g.T, 256, 0, s>>>(g.meta, g.d_leaves, g.d_tree_leaf0, g.d_tree_sing, nullptr, g.d_leaf_geo, g.D,
+                                        g.N, f, with_flux ? g.d_bc : nullptr, g.d_tree_c);
+        const int blocks = (int)std::min<long long>(((long long)g.n_leaf_boxes * C + 255) / 256, 152LL * 16);
+        k_tree_shift<<<blocks, 256, 0, s>>>(g.meta, g.d_leaves, g.n_leaf_boxes, C, f, g.d_tree_c);
+        g_launches += 2;
+        check(cudaGetLastError(), "k_tree_vsum");
+        return;
+    }
     const int nb = std::min(kSumBlocks, g.n_leaf_boxes);
     static_assert(3 * kSumBlocks <= kPartials, "partials buffer");
     k_leaf_vsum<<<nb, 256, 0, s>>>(g.meta, g.d_leaves, g.n_leaf_boxes, g.d_leaf_geo, g.D, g.N, f,

@@ -56,13 +56,42 @@ def test_singular_solve_and_mixed(types):
     assert rel_diff(b.get_solution(), a.get_solution()) <= 1e-8
 
 
+@pytest.mark.parametrize("precision", [afgpu.AFG_FP64, afgpu.AFG_MIXED])
+def test_forest_of_singular_and_dirichlet_trees(precision):
+    """A forest of singular trees (Neumann, periodic, mixed sides) and a
+    Dirichlet tree: each singular tree's source is made compatible and its
+    solution kept at zero mean on its own, as the oracle does per tree."""
+    specs = [([1, 1, 1, 1], 920), ([2, 2, 2, 2], 921), ([2, 2, 1, 1], 922), ([0, 1, 0, 1], 923)]
+    pairs = [singular_pair(2, 8, 2, 2, seed, types) for types, seed in specs]
+    f = afgpu.Forest([p[1] for p in pairs])
+    f.set_rhs(torch.tensor(np.concatenate([p[2] for p in pairs]), device="cuda"))
+    f.set_dirichlet(torch.tensor(np.concatenate([p[3] for p in pairs]), device="cuda"))
+    st = f.solve(afgpu.default_opts(rel_tol=1e-10, max_cycles=80, precision=precision))
+    u = f.get_solution().cpu().numpy()
+    off = 0
+    for k, (a, _, rho, bv) in enumerate(pairs):
+        a.set_rhs(rho); a.set_dirichlet(bv); a.zero_solution()
+        n = a.n_leaf_cells
+        assert st[k]["rel_residual"] <= 1e-10, k
+        if precision == afgpu.AFG_FP64:
+            ca = a.solve(1e-10, 80)
+            assert st[k]["cycles"] == ca, (k, st[k]["cycles"], ca)
+            assert rel_diff(u[off:off + n], a.get_solution()) <= TOL64, k
+        else:
+            a.solve(1e-12, 100)
+            assert rel_diff(u[off:off + n], a.get_solution()) <= 1e-8, k
+        off += n
+
+
 def test_singular_trees_are_refused_where_not_built():
     t = afgpu.Tree(2, 8, 3)
     t.set_boundary_types([1, 1, 1, 1])
     t.refine_uniform(2)
     n = t.n_leaf_cells
     with pytest.raises(afgpu.AfgError) as e:
-        afgpu.Forest([t, afgpu.Tree(2, 8, 3)])
+        s = afgpu.Tree(2, 8, 3, roots=(2, 1))
+        s.set_boundary_types([1, 1, 1, 1])
+        afgpu.Forest([t, s])
     assert e.value.code == afgpu.AFG_ERR_STATE
     t.set_rhs(torch.ones(n, dtype=torch.float64, device="cuda"))
     with pytest.raises(afgpu.AfgError) as e:
