@@ -373,30 +373,38 @@ def bench_blobs3d(K, W_, dev):
     ustar = torch.tensor(1e-4 * W.blobs3d(seed=2).rho(x), device=dev)
     h = torch.tensor(1.0 / (8 * 2.0 ** (np.repeat(t.leaf_levels(), 512) - 1)), device=dev)
     vol = h ** 3
-    opts = afgpu.default_opts(rel_tol=1e-10)
     rho = torch.tensor(rho_h, device=dev, requires_grad=True)
     b = torch.tensor(b_h, device=dev, requires_grad=True)
-    fwd, bwd = [], []
-    for i in range(W_ + K):
-        rho.grad = None
-        b.grad = None
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        torch.cuda.synchronize()
-        e[0].record()
-        u = PoissonSolve.apply(rho, b, t, opts, opts)
-        loss = 0.5 * (vol * (u - ustar) ** 2).sum()
-        e[1].record()
-        loss.backward()
-        e[2].record()
-        torch.cuda.synchronize()
-        if i >= W_:
-            fwd.append(e[0].elapsed_time(e[1]))
-            bwd.append(e[1].elapsed_time(e[2]))
-    f, bk = sum(fwd) / K, sum(bwd) / K
+
+    def run(opts):
+        fwd, bwd = [], []
+        for i in range(W_ + K):
+            rho.grad = None
+            b.grad = None
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            e[0].record()
+            u = PoissonSolve.apply(rho, b, t, opts, opts)
+            loss = 0.5 * (vol * (u - ustar) ** 2).sum()
+            e[1].record()
+            loss.backward()
+            e[2].record()
+            torch.cuda.synchronize()
+            if i >= W_:
+                fwd.append(e[0].elapsed_time(e[1]))
+                bwd.append(e[1].elapsed_time(e[2]))
+        return sum(fwd) / K, sum(bwd) / K, rho.grad.clone()
+
+    f, bk, g64 = run(afgpu.default_opts(rel_tol=1e-10))
+    fm, bkm, gmx = run(afgpu.default_opts(rel_tol=1e-10, precision=afgpu.AFG_MIXED))
     return {"workload": "3D octree, boxes 8^3, uniform 128^3 + 1 level where |rho| > 0.1 max|rho|, 8 Gaussian blobs "
                         "(s=0.03); loss = 0.5 sum vol (u - u*)^2; forward solve and adjoint solve to 1e-10",
             "unknowns": t.n_leaf_cells, "forward_ms": f, "backward_ms": bk, "fwd_bwd_ms": f + bk,
-            "unit": "ms per forward+backward", "grad_norm_rho": float(rho.grad.abs().max())}
+            "unit": "ms per forward+backward", "grad_norm_rho": float(g64.abs().max()),
+            "mixed": {"forward_ms": fm, "backward_ms": bkm, "fwd_bwd_ms": fm + bkm,
+                      "grad_rel_diff_vs_fp64": float((gmx - g64).abs().max() / g64.abs().max()),
+                      "note": "FP32 multigrid inside FP64 defect correction (forward) and as the FP64 "
+                              "BiCGStab's preconditioner (backward), both to 1e-10"}}
 
 
 def bench_paper_cmp(K, W_, dev):

@@ -315,7 +315,9 @@ int afg_residual_norm(afg_tree *t, double *max_abs_r, double *max_abs_rho);
  * for the transposed composite operator (FP64) and return lambda = dL/drho
  * (leaf cells) and dL/db = -(2/h^2) lambda (Dirichlet side) or -(1/h) lambda
  * (Neumann side) at the boundary-adjacent cell of every leaf boundary face.
- * Output pointers may be NULL. */
+ * BiCGStab with the preconditioner W M W^-1 (M one V-cycle, W the cell
+ * volumes); opts->precision AFG_MIXED runs M in FP32 (K^T, the recurrences
+ * and the tolerance stay FP64).  Output pointers may be NULL. */
 int afg_adjoint(afg_tree *t, const double *g_leaf_dev, double *lambda_leaf_dev,
                 double *dL_db_face_dev, const afg_mg_opts *opts, afg_stats *stats);
 

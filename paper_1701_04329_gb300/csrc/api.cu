@@ -323,19 +323,30 @@ int adjoint_solve(Grid &g, const afg_mg_opts &o, cudaStream_t s, const double *g
         return host_scalar(g, s);
     };
     const size_t bytes = (size_t)g.ncell * 8;
+    // AFG_MIXED: M is one FP32 V-cycle (the BiCGStab recurrences and K^T stay FP64)
+    const bool m32 = o.precision == AFG_MIXED;
+    if (m32) g.ensure_mixed();
     auto precond = [&](const double *in, double *out, cudaStream_t cs) {
         afg::launch_leaf_scale(g.leaf_cfg(true, cs), A, g.d_hb, L, n, g.wsadj.rho->as<double>(), in, -1);
-        g.leaf_rho_hat(g.wsadj, cs);
-        check(cudaMemsetAsync(g.wsadj.u->p, 0, bytes, cs), "zero");
-        g.vcycle(g.wsadj, g.lmax, mo, 1, nullptr, cs);
+        if (m32) {
+            afg::launch_to_f32(g.wsadj.rho->as<double>(), g.ws32.rho->as<float>(), g.ncell, cs);
+            check(cudaMemsetAsync(g.ws32.u->p, 0, (size_t)g.ncell * 4, cs), "zero");
+            g.vcycle(g.ws32, g.lmax, mo, 1, nullptr, cs);
+            afg::launch_to_f64(g.ws32.u->as<float>(), g.wsadj.u->as<double>(), g.ncell, cs);
+        } else {
+            g.leaf_rho_hat(g.wsadj, cs);
+            check(cudaMemsetAsync(g.wsadj.u->p, 0, bytes, cs), "zero");
+            g.vcycle(g.wsadj, g.lmax, mo, 1, nullptr, cs);
+        }
         afg::launch_leaf_scale(g.leaf_cfg(true, cs), A, g.d_hb, L, n, out, g.wsadj.u->as<double>(), 1);
     };
     auto apply_T = [&](const double *in, double *out) {
         afg::launch_adjoint_apply(lc, A, g.d_child, g.d_hb, L, n, in, out);
     };
     // graphs for the two preconditioner applications (fixed buffers)
-    auto P_p = [&]() { run(g, {20, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(p, ph, cs); }); };
-    auto P_s = [&]() { run(g, {21, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(sv, sh, cs); }); };
+    const int kp = m32 ? 22 : 20;
+    auto P_p = [&]() { run(g, {kp, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(p, ph, cs); }); };
+    auto P_s = [&]() { run(g, {kp + 1, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(sv, sh, cs); }); };
 
     const double bnorm = amax(bvec);
     check(cudaMemsetAsync(x, 0, bytes, s), "zero");

@@ -209,5 +209,7 @@ void launch_flag(const Grid &g, const double *f, int power, double tau_ref, doub
 void launch_leaf_center(const Grid &g, double *f, bool with_flux, cudaStream_t s);
 // dst = (float) src, n values
 void launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
+// dst = (double) src, n values
+void launch_to_f64(const float *src, double *dst, long long n, cudaStream_t s);
 
 }  // namespace afg

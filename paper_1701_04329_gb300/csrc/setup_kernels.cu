@@ -145,11 +145,24 @@ __global__ void k_tree_shift(BoxMeta A, const int *leaves, int nleaf, int C, dou
     }
 }
 
+__global__ void k_to_f64(const float *src, double *dst, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        dst[q] = (double)src[q];
+}
+
 __global__ void k_to_f32(const double *src, float *dst, long long n) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
         dst[q] = (float)src[q];
 }
 }  // namespace
+
+void launch_to_f64(const float *src, double *dst, long long n, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    k_to_f64<<<blocks, 256, 0, s>>>(src, dst, n);
+    ++g_launches;
+    check(cudaGetLastError(), "k_to_f64");
+}
 
 void launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s) {
     if (n <= 0) return;

@@ -32,6 +32,22 @@ def test_adjoint_matches_transpose_solve(D, N, uni, extra, seed):
     assert np.abs(lam - lo).max() <= 1e-9 * np.abs(lo).max()
 
 
+@pytest.mark.parametrize("D,N,uni,extra,seed", [(2, 8, 1, 3, 55), (3, 8, 1, 2, 56)])
+def test_adjoint_with_fp32_preconditioner(D, N, uni, extra, seed):
+    """AFG_MIXED: the preconditioner's V-cycle in FP32, K^T and the
+    BiCGStab recurrences in FP64 -- the same lambda at the same FP64
+    tolerance."""
+    a, b, rho, bv = pair_random(D, N, uni, extra, seed)
+    g = np.random.default_rng(seed).normal(size=a.n_leaf_cells)
+    ref = oadj.direct(a, g)
+    lam, db, st = b.adjoint(torch.tensor(g, device="cuda"),
+                            afgpu.default_opts(rel_tol=1e-12, max_cycles=100, precision=afgpu.AFG_MIXED))
+    assert st["rel_residual"] <= 1e-12
+    assert np.abs(lam.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+    dref = oadj.dl_db(a, ref)
+    assert np.abs(db.cpu().numpy() - dref).max() <= 1e-9 * np.abs(dref).max()
+
+
 def test_uniform_adjoint_equals_forward_solve():
     """On a uniform tree K is symmetric: K^T lam = g is the forward problem
     with rho = g and b = 0."""
