@@ -345,8 +345,12 @@ int adjoint_solve(Grid &g, const afg_mg_opts &o, cudaStream_t s, const double *g
     };
     // graphs for the two preconditioner applications (fixed buffers)
     const int kp = m32 ? 22 : 20;
-    auto P_p = [&]() { run(g, {kp, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(p, ph, cs); }); };
-    auto P_s = [&]() { run(g, {kp + 1, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(sv, sh, cs); }); };
+    auto P_p = [&]() {
+        run(g, {kp, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(p, ph, cs); });
+    };
+    auto P_s = [&]() {
+        run(g, {kp + 1, o.n_down, o.n_up, o.n_base, 0}, o.use_graph, s, [&](cudaStream_t cs) { precond(sv, sh, cs); });
+    };
 
     const double bnorm = amax(bvec);
     check(cudaMemsetAsync(x, 0, bytes, s), "zero");
